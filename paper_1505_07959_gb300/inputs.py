@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module builds matrices and nothing else: it holds none of the method's
+arithmetic (no flow, no time stepping, no parareal step).  Both the CUDA path
+and the CPU oracle receive the arrays made here as plain inputs.
+
+Every matrix is A = Q diag(lam) Q^T with Q Haar-random orthogonal: the QR
+factorisation of an n x n standard Gaussian matrix with the signs of R's
+diagonal moved into Q (so Q is Haar distributed), formed in float64 and
+symmetrised as (A + A^T)/2.  The spectra follow the matrix families of the
+workloads:
+
+* inverse flow (Example 1 of the paper, dQ/dt = Q(I-A)Q): lam ~ U[0.5, 2];
+* exponential flow (Example 2, dQ/dt = AQ): lam ~ U[-4, 0];
+* square-root steady state (dX/dt = A - X^2): lam log-uniform in [1e-3, 1];
+* inverse flow, wider spectrum: lam log-uniform in [1e-2, 1].
+
+The 1D Laplacian of the paper's Examples 1 and 2 is generated from its
+definition as well (tridiag(-1, 2, -1), optionally scaled by 1/h^2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+FLOW_INV = 0
+FLOW_EXP = 1
+FLOW_SQRT = 2
+FLOW_NAMES = {FLOW_INV: "inv", FLOW_EXP: "exp", FLOW_SQRT: "sqrt"}
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    """PCG64 generator for one problem; problem p of a batch uses seed base + p."""
+    return np.random.default_rng(int(seed))
+
+
+def haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-random orthogonal n x n matrix (QR of a Gaussian, R diagonal made positive)."""
+    z = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(z)
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    return q * d[None, :]
+
+
+def spectrum(n: int, kind: str, rng: np.random.Generator) -> np.ndarray:
+    """Eigenvalues for one matrix family (see the module docstring)."""
+    if kind == "inv":
+        return rng.uniform(0.5, 2.0, n)
+    if kind == "exp":
+        return rng.uniform(-4.0, 0.0, n)
+    if kind == "sqrt":
+        return np.exp(rng.uniform(math.log(1e-3), math.log(1.0), n))
+    if kind == "inv_wide":
+        return np.exp(rng.uniform(math.log(1e-2), math.log(1.0), n))
+    raise ValueError(f"unknown spectrum kind {kind!r}")
+
+
+@dataclasses.dataclass
+class SymMatrix:
+    """A symmetric test matrix with its generating eigen-decomposition."""
+
+    A: np.ndarray      # (n, n) float64, symmetric
+    Q: np.ndarray      # (n, n) float64, orthogonal
+    lam: np.ndarray    # (n,) float64
+
+
+def sym_matrix(n: int, kind: str, seed: int) -> SymMatrix:
+    """A = Q diag(lam) Q^T, float64, symmetrised."""
+    rng = rng_for(seed)
+    q = haar_orthogonal(n, rng)
+    lam = spectrum(n, kind, rng)
+    a = (q * lam[None, :]) @ q.T
+    a = 0.5 * (a + a.T)
+    return SymMatrix(A=np.ascontiguousarray(a), Q=q, lam=lam)
+
+
+def laplacian_1d(n: int, scaled: bool = True) -> np.ndarray:
+    """tridiag(-1, 2, -1) of order n, times 1/h^2 with h = 1/(n+1) when `scaled`."""
+    a = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    if scaled:
+        a *= float(n + 1) ** 2
+    return a
+
+
+@dataclasses.dataclass
+class Workload:
+    """One parareal problem: flow, matrix family, slices and step counts."""
+
+    name: str
+    flow: int
+    n: int
+    kind: str
+    T: float
+    N: int            # time slices
+    m: int            # forward-Euler substeps of the coarse propagator per slice
+    J: int            # RK4 steps of the fine propagator per slice
+    K_max: int        # maximum parareal iterations (fine sweeps after Step 0)
+    tol: float        # stop when max_n ||U^{k+1}_n - U^k_n||_F / ||U^{k+1}_n||_F < tol
+    seed: int = 0
+
+
+# The five workloads, named by what they are.
+INV_N64 = Workload("inverse flow, n=64, lam~U[0.5,2], N=8, J=16, fp64", FLOW_INV, 64, "inv",
+                   1.0, 8, 1, 16, 8, 1e-10)
+EXP_N2048 = Workload("exp flow, n=2048, lam~U[-4,0], N=64, J=64", FLOW_EXP, 2048, "exp",
+                     1.0, 64, 1, 64, 64, 1e-10)
+SQRT_N4096 = Workload("sqrt steady state, n=4096, lam~logU[1e-3,1], T=20, N=128, J=32",
+                      FLOW_SQRT, 4096, "sqrt", 20.0, 128, 1, 32, 128, 1e-10)
+INV_N1024_WIDE = Workload("inverse flow, n=1024, lam~logU[1e-2,1], N=64, J=64", FLOW_INV,
+                          1024, "inv_wide", 1.0, 64, 1, 64, 64, 1e-8)
+
+
+def batched_problems(count: int = 512, n_lo: int = 32, n_hi: int = 512, base_seed: int = 0):
+    """Mixed batch: n log-uniform in [n_lo, n_hi], flows cycling inv/exp/sqrt.
+
+    Square-root problems integrate to T=20 with two Euler substeps per coarse
+    slice (one substep of length 1.25 is unstable); the others use T=1 and one.
+    Returns a list of (Workload, SymMatrix).
+    """
+    rng = rng_for(base_seed + 1_000_003)
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))
+    out = []
+    for p in range(count):
+        n = int(round(ns[p]))
+        flow = p % 3
+        if flow == FLOW_SQRT:
+            w = Workload(f"batch[{p}] sqrt n={n}", FLOW_SQRT, n, "sqrt", 20.0, 16, 2, 32, 16, 1e-6,
+                         base_seed + p)
+        elif flow == FLOW_EXP:
+            w = Workload(f"batch[{p}] exp n={n}", FLOW_EXP, n, "exp", 1.0, 16, 1, 32, 16, 1e-6,
+                         base_seed + p)
+        else:
+            w = Workload(f"batch[{p}] inv n={n}", FLOW_INV, n, "inv", 1.0, 16, 1, 32, 16, 1e-6,
+                         base_seed + p)
+        out.append((w, sym_matrix(n, w.kind, w.seed)))
+    return out
