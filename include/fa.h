@@ -1,0 +1,193 @@
+/*
+ * fa.h -- C ABI of the parareal matrix-function library (GB300, sm_103a).
+ *
+ * The library evaluates f(A) as the state of a matrix ODE dX/dt = Fl(X),
+ * X(0) = X0, integrated by the classical parareal method (Algorithm 1 of
+ * Chehab & Petcu, "Parallel Matrix Function Evaluation via Initial value ODE
+ * modelling"):
+ *
+ *   FA_FLOW_INV   dX/dt = X (I - A) X, X(0) = I, X(1) = A^{-1}
+ *                 (Section 2, Example 1, eq. eqQ);
+ *   FA_FLOW_EXP   dX/dt = A X,         X(0) = I, X(1) = exp(A)
+ *                 (Section 2, Example 2);
+ *   FA_FLOW_SQRT  dX/dt = A - X^2,     X(0) = I, X(inf) = A^{1/2} for SPD A
+ *                 (an instance of the steady-state framework, eq. "stat" of
+ *                 the introduction and Section 4).
+ *
+ * The time interval [0, T] is cut into N uniform slices T_n = n T / N.  The
+ * fine propagator F runs J classical RK4 steps per slice, the coarse
+ * propagator G runs m forward-Euler substeps per slice, and each parareal
+ * iteration is: F on all N slices at once (the parallel step of Algorithm 1),
+ * then the sequential correction U_{n+1} = G(U^new_n) + F(U^old_n) - G(U^old_n)
+ * (eq. eqStepk+1), then the convergence test
+ * max_n ||U^{k+1}_n - U^k_n||_F / ||U^{k+1}_n||_F < tol.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Matrices at the boundary are float64, row-major, n x n, contiguous
+ *   (leading dimension n).  Arrays of matrices are batch-major [count][n][n].
+ * - Pointers named d* are device pointers (any CUDA allocation of the current
+ *   device, e.g. PyTorch tensors); pointers named h* are host pointers.  The
+ *   caller owns all of them; the library never frees them.
+ * - All work is enqueued on the plan's stream.  fa_parareal_solve* synchronise
+ *   that stream (they read the convergence scalar every iteration);
+ *   fa_fine_sweep, fa_coarse_sweep, fa_plan_set_matrix and fa_refine are
+ *   asynchronous and report device-side failures on the next synchronising
+ *   call.
+ * - Nothing is thrown across the ABI.  Every call returns an fa_status; on
+ *   failure, fa_last_error() (thread-local) holds a one-line explanation.
+ * - A plan owns no device memory except the workspace that the caller binds
+ *   with fa_plan_bind_workspace (the library calls no cudaMalloc).
+ * - Mixed-precision forms (FA_BF16*) use BF16 tensor-core products with
+ *   float32 accumulation, a double-float32 (hi + lo) RK4 state, and float64
+ *   for the parareal correction, the coarse-state additions and the norms.
+ */
+#ifndef FA_H
+#define FA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FA_OK = 0,
+  FA_ERR_ARG = 1,            /* invalid argument (sizes, pointers, enum values) */
+  FA_ERR_CUDA = 2,           /* a CUDA runtime/driver call failed */
+  FA_ERR_WORKSPACE = 3,      /* no workspace bound, or the bound one is too small */
+  FA_ERR_NONFINITE = 4,      /* a NaN/Inf appeared in the iterates or the inputs */
+  FA_ERR_NOT_CONVERGED = 5,  /* max_iters reached; the output is still written */
+  FA_ERR_TIMEOUT = 6,        /* a device-side wait gave up (error flag set by a kernel) */
+  FA_ERR_UNSUPPORTED = 7     /* valid but not supported (e.g. device is not sm_103) */
+} fa_status;
+
+typedef enum { FA_FLOW_INV = 0, FA_FLOW_EXP = 1, FA_FLOW_SQRT = 2 } fa_flow;
+
+/* Arithmetic of the fine and coarse propagators' matrix products.
+ * FA_F64     float64 everywhere (SIMT FMA).
+ * FA_BF16    one BF16 product per GEMM (operands rounded to BF16).
+ * FA_BF16X3  operands split into BF16 terms x = x0 + x1 (+ ...); products
+ *            x0y0 + x0y1 + x1y0.
+ * FA_BF16X4  products x0y0 + x0y1 + x1y0 + x2y0 (left operand to three terms).
+ * FA_BF16X6  every product xa yb with a + b <= 2.
+ * All BF16 forms accumulate in float32 on the tensor cores (tcgen05). */
+typedef enum {
+  FA_F64 = 0,
+  FA_BF16 = 1,
+  FA_BF16X3 = 2,
+  FA_BF16X4 = 3,
+  FA_BF16X6 = 4
+} fa_dtype;
+
+typedef struct {
+  int n;              /* matrix order, 1 <= n <= 16384 */
+  int flow;           /* fa_flow */
+  double T;           /* horizon, > 0 (Examples 1 and 2 use T = 1) */
+  int N;              /* number of time slices, >= 1 */
+  int coarse_steps;   /* m: forward-Euler substeps of G per slice, >= 1 */
+  int fine_steps;     /* J: RK4 steps of F per slice, >= 1 */
+  int max_iters;      /* K: maximum parareal iterations (fine sweeps after Step 0), >= 0 */
+  double tol;         /* stop when max_n ||dU_n||_F / ||U_n||_F < tol (0 = run all K) */
+  int fine_dtype;     /* fa_dtype of F */
+  int coarse_dtype;   /* fa_dtype of G (FA_F64, or the same BF16 form as F) */
+  int refine_steps;   /* float64 refinement steps on the result (inverse: Newton-Schulz); 0 = none */
+} fa_problem_desc;
+
+typedef struct {
+  int iters;           /* fine sweeps performed */
+  int converged;       /* 1 if the tolerance was reached */
+  double last_dx;      /* max_n ||dU_n||_F / ||U_n||_F of the last iteration */
+  double t_init_ms;    /* matrix set-up + Step 0 */
+  double t_fine_ms;    /* all fine sweeps */
+  double t_coarse_ms;  /* all coarse sweeps (with correction and norms) */
+  double t_refine_ms;  /* refinement */
+  double *dx_history;  /* caller-owned host array of max_iters doubles, or NULL */
+} fa_report;
+
+typedef struct fa_plan_s *fa_plan_t;
+
+/* Create a plan for one problem shape.  Validates the descriptor (FA_ERR_ARG
+ * on n < 1, N < 1, J < 1, m < 1, T <= 0, K < 0, unknown flow or dtype) and
+ * checks that the current device is sm_103 (FA_ERR_UNSUPPORTED otherwise).
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  On success
+ * *out receives the plan and *workspace_bytes the device workspace size the
+ * plan needs; bind it before any compute call.  No device memory is
+ * allocated. */
+fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream,
+                  size_t *workspace_bytes);
+
+/* Bind caller-allocated device memory (>= the size fa_plan returned, 256-byte
+ * aligned) as the plan's workspace.  The memory must stay valid until the plan
+ * is destroyed or another workspace is bound.  FA_ERR_WORKSPACE if too small
+ * or misaligned. */
+fa_status fa_plan_bind_workspace(fa_plan_t p, void *d_workspace, size_t bytes);
+
+/* Load A (device, n x n row-major float64) into the plan: builds the operand
+ * forms the propagators use (BF16 terms of A or of I - A, transposes).  Must
+ * precede fa_fine_sweep / fa_coarse_sweep / fa_refine; fa_parareal_solve
+ * calls it itself.  A may be freed afterwards. */
+fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA);
+
+/* Fine propagator on every slice at once (the parallel step of Algorithm 1):
+ * dF[b] = F(T_{b+1}, T_b, dU[b]) for b = 0..N-1, i.e. J RK4 steps of size
+ * T/(N J) from dU[b].  dU and dF are [N][n][n] float64 device arrays; they
+ * must not overlap. */
+fa_status fa_fine_sweep(fa_plan_t p, const double *dU, double *dF);
+
+/* Coarse sweep with correction (the sequential part of Algorithm 1):
+ *   V_0 = dU0;  for n = 0..N-1:  G_n = G(V_n),  V_{n+1} = G_n + D_n,
+ * with D_n = dD[n] (pass dD = NULL for Step 0, eq. eqStep0: V_{n+1} = G_n).
+ * Writes dUnew[0..N] = V ([N+1][n][n]) and dGnew[0..N-1] = G_n ([N][n][n]).
+ * If dNorms is not NULL, dUold ([N+1][n][n], the previous iterate; it may be
+ * the same array as dUnew, read before overwritten) must be given and
+ * dNorms[2n], dNorms[2n+1] (float64, device, [N][2]) receive
+ * ||V_{n+1} - Uold_{n+1}||_F^2 and ||V_{n+1}||_F^2, summed in a fixed order
+ * (bitwise reproducible). */
+fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD,
+                          double *dUnew, double *dGnew, double *dNorms,
+                          const double *dUold);
+
+/* Float64 refinement of dX in place (inverse flow: `refine_steps`
+ * Newton-Schulz steps X <- X (2I - A X)).  FA_ERR_UNSUPPORTED for flows
+ * without a refinement. */
+fa_status fa_refine(fa_plan_t p, double *dX);
+
+/* Whole solve on device buffers: set A, Step 0, up to max_iters parareal
+ * iterations, optional refinement; dXout (n x n) receives U_N.  dX0 = NULL
+ * means X0 = I.  Returns FA_ERR_NOT_CONVERGED (with dXout written) when the
+ * tolerance was not met.  `report` may be NULL. */
+fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0,
+                            double *dXout, fa_report *report);
+
+/* The same solve on HOST buffers (pageable or pinned): copies hA (and hX0)
+ * into the workspace, solves, and copies U_N back into hXout. */
+fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX0,
+                                 double *hXout, fa_report *report);
+
+/* Diagnostic: one matrix product dC = dL * dR (n x n, device, row-major
+ * float64) through the plan's coarse arithmetic (the BF16 term products on
+ * the tensor cores for FA_BF16* coarse dtypes, float64 otherwise), without
+ * any epilogue arithmetic.  Mixed forms need a flow with an L-form operand
+ * buffer (FA_FLOW_INV or FA_FLOW_SQRT); FA_ERR_UNSUPPORTED otherwise. */
+fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, double *dC);
+
+/* Release the plan (not the workspace, which the caller owns). */
+fa_status fa_plan_destroy(fa_plan_t p);
+
+/* Static description of a status code. */
+const char *fa_status_string(fa_status s);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *fa_last_error(void);
+
+/* Number of kernels the library launched on this thread since the last reset
+ * (diagnostics for launch counting); fa_launch_count_reset sets it to 0. */
+unsigned long long fa_launch_count(void);
+void fa_launch_count_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FA_H */

@@ -1,0 +1,743 @@
+// Host driver and C ABI of libfa: plans, workspace layout, the fine and
+// coarse sweeps of classical parareal (Algorithm 1) and the solve loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fa_internal.h"
+#include "fa_ptx.cuh"
+
+using fa::EpiParams;
+using fa::F64GemmParams;
+using fa::TcGemmParams;
+
+namespace {
+
+thread_local std::string g_last_error;
+thread_local unsigned long long g_launches = 0;
+
+fa_status set_err(fa_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+fa_status set_err(fa_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define FA_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(FA_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                     __FILE__, __LINE__);                                                 \
+  } while (0)
+
+#define FA_TRY(call)              \
+  do {                            \
+    fa_status s_ = (call);        \
+    if (s_ != FA_OK) return s_;   \
+  } while (0)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool is_mixed(int dt) { return dt >= FA_BF16 && dt <= FA_BF16X6; }
+
+// Bump allocator over the workspace (256-byte aligned sub-buffers).  With a
+// null base it only measures.
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+namespace fa {
+void count_launch() { ++g_launches; }
+}  // namespace fa
+
+struct fa_plan_s {
+  fa_problem_desc d{};
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  bool mixed = false, cmixed = false;
+  fa::PairSet ps{};
+  int ldp = 0;
+  size_t nn = 0;
+  size_t ws_need = 0;
+  char *ws = nullptr;
+  bool matrix_set = false;
+
+  // parareal state (float64 row-major)
+  double *U = nullptr, *Gold = nullptr, *Gnew = nullptr, *D = nullptr;
+  double *part = nullptr, *norms = nullptr, *dx = nullptr;
+  double *Vtmp[2] = {nullptr, nullptr};
+  double *A64 = nullptr, *B64 = nullptr, *Xin = nullptr, *Xout = nullptr, *R1 = nullptr,
+         *R2 = nullptr;
+  int *err = nullptr;
+  int part_tiles = 0;   // partial-norm slots per slice
+
+  // mixed fine state
+  float *x_hi = nullptr, *x_lo = nullptr, *acc = nullptr, *a_hi = nullptr, *a_lo = nullptr;
+  __nv_bfloat16 *Aop = nullptr, *Yl[2] = {nullptr, nullptr}, *Yr[2] = {nullptr, nullptr},
+                *Pr = nullptr;
+  // mixed coarse operands (single slice)
+  __nv_bfloat16 *Vl[2] = {nullptr, nullptr}, *Vr[2] = {nullptr, nullptr}, *Pcr = nullptr;
+  size_t strideY = 0, strideV = 0, strideA = 0;   // elements between terms
+  // float64 fine state
+  double *X64 = nullptr, *acc64 = nullptr, *Y64[2] = {nullptr, nullptr}, *P64 = nullptr,
+         *Pc64 = nullptr;
+
+  CUtensorMap tmA{}, tmYl[2]{}, tmYr[2]{}, tmPr{}, tmVl[2]{}, tmVr[2]{}, tmPcr{};
+
+  bool needs_l() const { return d.flow != FA_FLOW_EXP; }  // Y in L form (left factor)
+};
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256;
+
+size_t carve(fa_plan_s *p, char *base) {
+  Carver c{base};
+  const fa_problem_desc &d = p->d;
+  const size_t nn = p->nn;
+  const size_t N = static_cast<size_t>(d.N);
+  p->U = c.take<double>((N + 1) * nn);
+  p->Gold = c.take<double>(N * nn);
+  p->Gnew = c.take<double>(N * nn);
+  p->D = c.take<double>(N * nn);
+  p->part = c.take<double>(N * static_cast<size_t>(p->part_tiles) * 2);
+  p->norms = c.take<double>(N * 2);
+  p->dx = c.take<double>(4);
+  p->err = c.take<int>(4);
+  if (d.coarse_steps > 1) {
+    p->Vtmp[0] = c.take<double>(nn);
+    p->Vtmp[1] = c.take<double>(nn);
+  }
+  p->A64 = c.take<double>(nn);
+  p->Xin = c.take<double>(nn);
+  p->Xout = c.take<double>(nn);
+  if (d.flow == FA_FLOW_INV && (!p->mixed || !p->cmixed)) p->B64 = c.take<double>(nn);
+  p->R1 = c.take<double>(nn);
+  p->R2 = c.take<double>(nn);
+  const size_t ldp = static_cast<size_t>(p->ldp);
+  const size_t tl = static_cast<size_t>(p->ps.terms_l), tr = static_cast<size_t>(p->ps.terms_r);
+  if (p->mixed || p->cmixed) {
+    p->strideA = static_cast<size_t>(d.n) * ldp;
+    if (d.flow != FA_FLOW_SQRT) p->Aop = c.take<__nv_bfloat16>(tl * p->strideA);
+    if (d.flow == FA_FLOW_SQRT) {
+      p->a_hi = c.take<float>(nn);
+      p->a_lo = c.take<float>(nn);
+    }
+  }
+  if (p->mixed) {
+    p->x_hi = c.take<float>(N * nn);
+    p->x_lo = c.take<float>(N * nn);
+    p->acc = c.take<float>(N * nn);
+    p->strideY = N * static_cast<size_t>(d.n) * ldp;
+    for (int k = 0; k < 2; ++k) {
+      p->Yr[k] = c.take<__nv_bfloat16>(tr * p->strideY);
+      if (p->needs_l()) p->Yl[k] = c.take<__nv_bfloat16>(tl * p->strideY);
+    }
+    if (d.flow == FA_FLOW_INV) p->Pr = c.take<__nv_bfloat16>(tr * p->strideY);
+  } else {
+    p->X64 = c.take<double>(N * nn);
+    p->acc64 = c.take<double>(N * nn);
+    p->Y64[0] = c.take<double>(N * nn);
+    p->Y64[1] = c.take<double>(N * nn);
+    if (d.flow == FA_FLOW_INV) p->P64 = c.take<double>(N * nn);
+  }
+  if (p->cmixed) {
+    p->strideV = static_cast<size_t>(d.n) * ldp;
+    for (int k = 0; k < 2; ++k) {
+      p->Vr[k] = c.take<__nv_bfloat16>(tr * p->strideV);
+      if (p->needs_l()) p->Vl[k] = c.take<__nv_bfloat16>(tl * p->strideV);
+    }
+    if (d.flow == FA_FLOW_INV) p->Pcr = c.take<__nv_bfloat16>(tr * p->strideV);
+  } else {
+    if (d.flow == FA_FLOW_INV) p->Pc64 = c.take<double>(nn);
+  }
+  return c.off + 256;
+}
+
+fa_status encode(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nterms,
+                 size_t term_stride, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_err(FA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[4] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n),
+                        static_cast<cuuint64_t>(nslices), static_cast<cuuint64_t>(nterms)};
+  cuuint64_t strides[3] = {static_cast<cuuint64_t>(ldp) * 2,
+                           static_cast<cuuint64_t>(n) * ldp * 2,
+                           static_cast<cuuint64_t>(term_stride) * 2};
+  cuuint32_t box[4] = {64, static_cast<cuuint32_t>(box_rows), 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_err(FA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return FA_OK;
+}
+
+fa_status encode_all(fa_plan_s *p) {
+  const int n = p->d.n, ldp = p->ldp, N = p->d.N;
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->Aop) FA_TRY(encode(&p->tmA, p->Aop, n, ldp, 1, tl, p->strideA, TC_BM));
+  if (p->mixed) {
+    for (int k = 0; k < 2; ++k) {
+      FA_TRY(encode(&p->tmYr[k], p->Yr[k], n, ldp, N, tr, p->strideY, TC_BN));
+      if (p->Yl[k]) FA_TRY(encode(&p->tmYl[k], p->Yl[k], n, ldp, N, tl, p->strideY, TC_BM));
+    }
+    if (p->Pr) FA_TRY(encode(&p->tmPr, p->Pr, n, ldp, N, tr, p->strideY, TC_BN));
+  }
+  if (p->cmixed) {
+    for (int k = 0; k < 2; ++k) {
+      FA_TRY(encode(&p->tmVr[k], p->Vr[k], n, ldp, 1, tr, p->strideV, TC_BN));
+      if (p->Vl[k]) FA_TRY(encode(&p->tmVl[k], p->Vl[k], n, ldp, 1, tl, p->strideV, TC_BM));
+    }
+    if (p->Pcr) FA_TRY(encode(&p->tmPcr, p->Pcr, n, ldp, 1, tr, p->strideV, TC_BN));
+  }
+  return FA_OK;
+}
+
+EpiParams base_epi(const fa_plan_s *p) {
+  EpiParams e;
+  memset(&e, 0, sizeof(e));
+  e.flow = p->d.flow;
+  e.n = p->d.n;
+  e.ldp = p->ldp;
+  e.err = p->err;
+  return e;
+}
+
+TcGemmParams tc_params(const fa_plan_s *p, int nb, int l_batched, int r_batched,
+                       const EpiParams &e) {
+  TcGemmParams g;
+  memset(&g, 0, sizeof(g));
+  g.n = p->d.n;
+  g.nb = nb;
+  g.l_batched = l_batched;
+  g.r_batched = r_batched;
+  g.mt = (p->d.n + TC_BM - 1) / TC_BM;
+  g.nt = (p->d.n + TC_BN - 1) / TC_BN;
+  g.num_tiles = g.mt * g.nt * nb;
+  g.kblocks = (p->d.n + 63) / 64;
+  g.npairs = p->ps.npairs;
+  for (int k = 0; k < g.npairs; ++k) {
+    g.pair_a[k] = p->ps.a[k];
+    g.pair_b[k] = p->ps.b[k];
+  }
+  g.idesc = fa::ptx::idesc_bf16_f32(TC_BM, TC_BN);
+  g.epi = e;
+  return g;
+}
+
+fa_status tc(const fa_plan_s *p, const CUtensorMap &L, const CUtensorMap &R, const TcGemmParams &g) {
+  FA_CUDA(fa::launch_tc_gemm(&L, &R, g, p->num_sms, p->stream));
+  return FA_OK;
+}
+
+fa_status f64(const fa_plan_s *p, const double *L, size_t ls, const double *R, size_t rs, int nb,
+              const EpiParams &e) {
+  F64GemmParams g;
+  memset(&g, 0, sizeof(g));
+  g.n = p->d.n;
+  g.nb = nb;
+  g.L = L;
+  g.R = R;
+  g.l_stride = ls;
+  g.r_stride = rs;
+  g.epi = e;
+  FA_CUDA(fa::launch_f64_gemm(g, p->stream));
+  return FA_OK;
+}
+
+fa_status check_ready(const fa_plan_s *p, bool need_matrix) {
+  if (!p) return set_err(FA_ERR_ARG, "null plan");
+  if (!p->ws) return set_err(FA_ERR_WORKSPACE, "no workspace bound");
+  if (need_matrix && !p->matrix_set)
+    return set_err(FA_ERR_ARG, "fa_plan_set_matrix has not been called");
+  return FA_OK;
+}
+
+// ---- fine sweep ------------------------------------------------------------------------------
+
+// F on every slice: out = F(U_b) (g_old == null) or F(U_b) - g_old_b.
+fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g_old) {
+  const fa_problem_desc &d = p->d;
+  const int n = d.n, N = d.N, J = d.fine_steps;
+  const size_t nn = p->nn;
+  const double h = d.T / static_cast<double>(N) / static_cast<double>(J);
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->mixed) {
+    FA_CUDA(fa::launch_load_state(U, N, n, p->ldp, p->x_hi, p->x_lo, p->Yl[0],
+                                  p->needs_l() ? tl : 0, p->strideY, p->Yr[0], tr, p->strideY,
+                                  p->stream));
+  } else {
+    FA_CUDA(cudaMemcpyAsync(p->X64, U, N * nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                            p->stream));
+    FA_CUDA(cudaMemcpyAsync(p->Y64[0], U, N * nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                            p->stream));
+  }
+  int cur = 0;
+  for (int j = 0; j < J; ++j) {
+    for (int s = 1; s <= 4; ++s) {
+      const bool last = (j == J - 1 && s == 4);
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_STAGE;
+      e.stage = s;
+      e.last = last ? 1 : 0;
+      e.h = h;
+      e.ch = (s == 3) ? h : (s < 3 ? 0.5 * h : 0.0);
+      e.f_out = out;
+      e.g_old = g_old;
+      if (p->mixed) {
+        e.x_hi = p->x_hi;
+        e.x_lo = p->x_lo;
+        e.acc = p->acc;
+        e.a_hi = p->a_hi;
+        e.a_lo = p->a_lo;
+        e.out_r = p->Yr[cur ^ 1];
+        e.out_l = p->Yl[cur ^ 1];
+        e.terms_r = tr;
+        e.terms_l = p->needs_l() ? tl : 0;
+        e.term_stride_r = e.term_stride_l = p->strideY;
+        if (d.flow == FA_FLOW_EXP) {
+          FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, N, 0, 1, e)));
+        } else if (d.flow == FA_FLOW_SQRT) {
+          FA_TRY(tc(p, p->tmYl[cur], p->tmYr[cur], tc_params(p, N, 1, 1, e)));
+        } else {
+          EpiParams e1 = base_epi(p);
+          e1.mode = fa::EPI_PROD;
+          e1.out_r = p->Pr;
+          e1.terms_r = tr;
+          e1.term_stride_r = p->strideY;
+          FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, N, 0, 1, e1)));
+          FA_TRY(tc(p, p->tmYl[cur], p->tmPr, tc_params(p, N, 1, 1, e)));
+        }
+      } else {
+        e.x64 = p->X64;
+        e.acc64 = p->acc64;
+        e.a64 = p->A64;
+        e.out64 = p->Y64[cur ^ 1];
+        const double *Y = p->Y64[cur];
+        if (d.flow == FA_FLOW_EXP) {
+          FA_TRY(f64(p, p->A64, 0, Y, nn, N, e));
+        } else if (d.flow == FA_FLOW_SQRT) {
+          FA_TRY(f64(p, Y, nn, Y, nn, N, e));
+        } else {
+          EpiParams e1 = base_epi(p);
+          e1.mode = fa::EPI_PROD;
+          e1.out64 = p->P64;
+          FA_TRY(f64(p, p->B64, 0, Y, nn, N, e1));
+          FA_TRY(f64(p, Y, nn, p->P64, nn, N, e));
+        }
+      }
+      cur ^= 1;
+    }
+  }
+  return FA_OK;
+}
+
+// ---- coarse sweep ----------------------------------------------------------------------------
+
+fa_status coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *Unew, double *Gout,
+                       double *norms, const double *Uold) {
+  const fa_problem_desc &d = p->d;
+  const int n = d.n, N = d.N, m = d.coarse_steps;
+  const size_t nn = p->nn;
+  const double dt = d.T / static_cast<double>(N) / static_cast<double>(m);
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (Unew != U0)
+    FA_CUDA(cudaMemcpyAsync(Unew, U0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  int cur = 0;
+  if (p->cmixed) {
+    FA_CUDA(fa::launch_split_terms(U0, 1, n, p->ldp, p->Vl[0], p->needs_l() ? tl : 0,
+                                   p->strideV, p->Vr[0], tr, p->strideV, 0, p->stream));
+  }
+  const int tiles = p->part_tiles;
+  for (int s = 0; s < N; ++s) {
+    for (int sub = 0; sub < m; ++sub) {
+      const bool last = (sub == m - 1);
+      const double *vin = (sub == 0) ? Unew + static_cast<size_t>(s) * nn : p->Vtmp[(sub - 1) & 1];
+      double *vout = last ? Unew + static_cast<size_t>(s + 1) * nn : p->Vtmp[sub & 1];
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_EULER;
+      e.dt = dt;
+      e.v_in = vin;
+      e.v_out = vout;
+      e.euler_last = last ? 1 : 0;
+      if (last) {
+        e.g_out = Gout + static_cast<size_t>(s) * nn;
+        e.d_in = D ? D + static_cast<size_t>(s) * nn : nullptr;
+        e.u_old = (norms && Uold) ? Uold + static_cast<size_t>(s + 1) * nn : nullptr;
+        e.norm_part = p->part + static_cast<size_t>(s) * tiles * 2;
+      }
+      if (p->cmixed) {
+        e.a_hi = p->a_hi;
+        e.a_lo = p->a_lo;
+        e.out_r = p->Vr[cur ^ 1];
+        e.out_l = p->Vl[cur ^ 1];
+        e.terms_r = tr;
+        e.terms_l = p->needs_l() ? tl : 0;
+        e.term_stride_r = e.term_stride_l = p->strideV;
+        if (d.flow == FA_FLOW_EXP) {
+          FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+        } else if (d.flow == FA_FLOW_SQRT) {
+          FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+        } else {
+          EpiParams e1 = base_epi(p);
+          e1.mode = fa::EPI_PROD;
+          e1.out_r = p->Pcr;
+          e1.terms_r = tr;
+          e1.term_stride_r = p->strideV;
+          FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e1)));
+          FA_TRY(tc(p, p->tmVl[cur], p->tmPcr, tc_params(p, 1, 0, 0, e)));
+        }
+        cur ^= 1;
+      } else {
+        e.a64 = p->A64;
+        if (d.flow == FA_FLOW_EXP) {
+          FA_TRY(f64(p, p->A64, 0, vin, 0, 1, e));
+        } else if (d.flow == FA_FLOW_SQRT) {
+          FA_TRY(f64(p, vin, 0, vin, 0, 1, e));
+        } else {
+          EpiParams e1 = base_epi(p);
+          e1.mode = fa::EPI_PROD;
+          e1.out64 = p->Pc64;
+          FA_TRY(f64(p, p->B64, 0, vin, 0, 1, e1));
+          FA_TRY(f64(p, vin, 0, p->Pc64, 0, 1, e));
+        }
+      }
+    }
+  }
+  if (norms && Uold) FA_CUDA(fa::launch_reduce_norms(p->part, N, tiles, norms, p->stream));
+  return FA_OK;
+}
+
+fa_status read_err(fa_plan_s *p) {
+  int h = 0;
+  FA_CUDA(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaStreamSynchronize(p->stream));
+  if (h == FA_ERR_TIMEOUT) return set_err(FA_ERR_TIMEOUT, "a device-side wait timed out");
+  if (h == FA_ERR_NONFINITE) return set_err(FA_ERR_NONFINITE, "non-finite values in the iterates");
+  if (h != 0) return set_err(static_cast<fa_status>(h), "device error %d", h);
+  return FA_OK;
+}
+
+fa_status refine(fa_plan_s *p, double *X) {
+  const fa_problem_desc &d = p->d;
+  if (d.refine_steps <= 0) return FA_OK;
+  if (d.flow != FA_FLOW_INV)
+    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+  for (int s = 0; s < d.refine_steps; ++s) {
+    // T = 2I - A X ; X <- X T  (Newton-Schulz)
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_STORE;
+    e.alpha = -1.0;
+    e.beta = 2.0;
+    e.store_out = p->R1;
+    FA_TRY(f64(p, p->A64, 0, X, 0, 1, e));
+    e.alpha = 1.0;
+    e.beta = 0.0;
+    e.store_out = p->R2;
+    FA_TRY(f64(p, X, 0, p->R1, 0, 1, e));
+    FA_CUDA(cudaMemcpyAsync(X, p->R2, p->nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                            p->stream));
+  }
+  return FA_OK;
+}
+
+}  // namespace
+
+// ---- C ABI -----------------------------------------------------------------------------------
+
+extern "C" {
+
+fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t *ws_bytes) {
+  if (!out || !d || !ws_bytes) return set_err(FA_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (d->n < 1 || d->n > 16384) return set_err(FA_ERR_ARG, "n = %d out of range [1, 16384]", d->n);
+  if (d->N < 1) return set_err(FA_ERR_ARG, "N = %d must be >= 1", d->N);
+  if (d->fine_steps < 1) return set_err(FA_ERR_ARG, "fine_steps = %d must be >= 1", d->fine_steps);
+  if (d->coarse_steps < 1)
+    return set_err(FA_ERR_ARG, "coarse_steps = %d must be >= 1", d->coarse_steps);
+  if (!(d->T > 0.0) || !std::isfinite(d->T)) return set_err(FA_ERR_ARG, "T must be finite and > 0");
+  if (d->max_iters < 0) return set_err(FA_ERR_ARG, "max_iters must be >= 0");
+  if (!(d->tol >= 0.0)) return set_err(FA_ERR_ARG, "tol must be >= 0");
+  if (d->flow < FA_FLOW_INV || d->flow > FA_FLOW_SQRT)
+    return set_err(FA_ERR_ARG, "unknown flow %d", d->flow);
+  if (d->fine_dtype < FA_F64 || d->fine_dtype > FA_BF16X6)
+    return set_err(FA_ERR_ARG, "unknown fine dtype %d", d->fine_dtype);
+  if (d->coarse_dtype != FA_F64 && d->coarse_dtype != d->fine_dtype)
+    return set_err(FA_ERR_ARG, "coarse dtype must be FA_F64 or the fine dtype");
+  if (d->refine_steps < 0) return set_err(FA_ERR_ARG, "refine_steps must be >= 0");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return set_err(FA_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  cudaDeviceProp prop;
+  ce = cudaGetDeviceProperties(&prop, dev);
+  if (ce != cudaSuccess)
+    return set_err(FA_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(ce));
+  if (prop.major != 10 || prop.minor != 3)
+    return set_err(FA_ERR_UNSUPPORTED, "device %s is sm_%d%d; this library is built for sm_103a",
+                   prop.name, prop.major, prop.minor);
+  fa_plan_s *p = new (std::nothrow) fa_plan_s();
+  if (!p) return set_err(FA_ERR_ARG, "out of host memory");
+  p->d = *d;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->device = dev;
+  p->num_sms = prop.multiProcessorCount;
+  p->mixed = is_mixed(d->fine_dtype);
+  p->cmixed = is_mixed(d->coarse_dtype);
+  p->ps = fa::pair_set(p->mixed ? d->fine_dtype : d->coarse_dtype);
+  p->ldp = (d->n + 7) / 8 * 8;
+  p->nn = static_cast<size_t>(d->n) * d->n;
+  p->part_tiles = p->cmixed ? ((d->n + TC_BM - 1) / TC_BM) * ((d->n + TC_BN - 1) / TC_BN)
+                            : fa::f64_tiles_per_slice(d->n, 1);
+  p->ws_need = carve(p, nullptr);
+  *ws_bytes = p->ws_need;
+  *out = p;
+  return FA_OK;
+}
+
+fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
+  if (!p) return set_err(FA_ERR_ARG, "null plan");
+  if (!ws) return set_err(FA_ERR_WORKSPACE, "null workspace");
+  if (bytes < p->ws_need)
+    return set_err(FA_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", bytes, p->ws_need);
+  if (reinterpret_cast<uintptr_t>(ws) & 255)
+    return set_err(FA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  p->ws = static_cast<char *>(ws);
+  carve(p, p->ws);
+  p->matrix_set = false;
+  FA_TRY(encode_all(p));
+  FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  return FA_OK;
+}
+
+fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA) {
+  FA_TRY(check_ready(p, false));
+  if (!dA) return set_err(FA_ERR_ARG, "null A");
+  const int n = p->d.n;
+  const size_t nn = p->nn;
+  if (dA != p->A64)
+    FA_CUDA(cudaMemcpyAsync(p->A64, dA, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  FA_CUDA(fa::launch_check_finite(p->A64, nn, p->err, p->stream));
+  if (p->B64) FA_CUDA(fa::launch_i_minus(p->A64, n, p->B64, p->stream));
+  if (p->mixed || p->cmixed) {
+    const int tl = p->ps.terms_l;
+    if (p->d.flow == FA_FLOW_EXP)
+      FA_CUDA(fa::launch_split_terms(p->A64, 1, n, p->ldp, p->Aop, tl, p->strideA, nullptr, 0, 0,
+                                     0, p->stream));
+    else if (p->d.flow == FA_FLOW_INV)
+      FA_CUDA(fa::launch_split_terms(p->A64, 1, n, p->ldp, p->Aop, tl, p->strideA, nullptr, 0, 0,
+                                     1, p->stream));
+    else
+      FA_CUDA(fa::launch_colmajor_pair(p->A64, n, p->a_hi, p->a_lo, p->stream));
+  }
+  p->matrix_set = true;
+  return FA_OK;
+}
+
+fa_status fa_fine_sweep(fa_plan_t p, const double *dU, double *dF) {
+  FA_TRY(check_ready(p, true));
+  if (!dU || !dF) return set_err(FA_ERR_ARG, "null pointer");
+  return fine_sweep(p, dU, dF, nullptr);
+}
+
+fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD, double *dUnew,
+                          double *dGnew, double *dNorms, const double *dUold) {
+  FA_TRY(check_ready(p, true));
+  if (!dU0 || !dUnew || !dGnew) return set_err(FA_ERR_ARG, "null pointer");
+  if (dNorms && !dUold) return set_err(FA_ERR_ARG, "dNorms requires dUold");
+  return coarse_sweep(p, dU0, dD, dUnew, dGnew, dNorms, dUold);
+}
+
+fa_status fa_refine(fa_plan_t p, double *dX) {
+  FA_TRY(check_ready(p, true));
+  if (!dX) return set_err(FA_ERR_ARG, "null pointer");
+  if (p->d.flow != FA_FLOW_INV)
+    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+  return refine(p, dX);
+}
+
+fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, double *dXout,
+                            fa_report *r) {
+  FA_TRY(check_ready(p, false));
+  if (!dA || !dXout) return set_err(FA_ERR_ARG, "null pointer");
+  if (p->d.refine_steps > 0 && p->d.flow != FA_FLOW_INV)
+    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+  const fa_problem_desc &d = p->d;
+  const size_t nn = p->nn;
+  cudaEvent_t ev[4];
+  for (auto &e : ev) FA_CUDA(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  FA_CUDA(cudaEventRecord(ev[0], p->stream));
+  FA_TRY(fa_plan_set_matrix(p, dA));
+  if (dX0) {
+    FA_CUDA(cudaMemcpyAsync(p->U, dX0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    FA_CUDA(fa::launch_identity(p->U, d.n, p->stream));
+  }
+  // Step 0 (eq. eqStep0): U^0_{n+1} = G(U^0_n), G(U^0_n) kept as G_old.
+  FA_TRY(coarse_sweep(p, p->U, nullptr, p->U, p->Gold, nullptr, nullptr));
+  FA_CUDA(cudaEventRecord(ev[1], p->stream));
+  FA_CUDA(cudaEventSynchronize(ev[1]));
+  float ms = 0.f;
+  FA_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+  double t_init = ms, t_fine = 0.0, t_coarse = 0.0, t_ref = 0.0;
+  int iters = 0;
+  bool converged = false;
+  double dx = INFINITY;
+  fa_status st = FA_OK;
+  for (int k = 0; k < d.max_iters; ++k) {
+    // Step k+1: the fine propagator on every slice at once, D_n = F(U^k_n) - G(U^k_n) ...
+    FA_CUDA(cudaEventRecord(ev[1], p->stream));
+    FA_TRY(fine_sweep(p, p->U, p->D, p->Gold));
+    FA_CUDA(cudaEventRecord(ev[2], p->stream));
+    // ... then the sequential correction U^{k+1}_{n+1} = G(U^{k+1}_n) + D_n (eq. eqStepk+1).
+    FA_TRY(coarse_sweep(p, p->U, p->D, p->U, p->Gnew, p->norms, p->U));
+    FA_CUDA(fa::launch_max_ratio(p->norms, d.N, p->dx, p->err, p->stream));
+    FA_CUDA(cudaEventRecord(ev[3], p->stream));
+    FA_CUDA(cudaMemcpyAsync(&dx, p->dx, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    FA_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+    t_fine += ms;
+    FA_CUDA(cudaEventElapsedTime(&ms, ev[2], ev[3]));
+    t_coarse += ms;
+    double *t = p->Gold;
+    p->Gold = p->Gnew;
+    p->Gnew = t;
+    ++iters;
+    if (r && r->dx_history) r->dx_history[k] = dx;
+    if (!std::isfinite(dx)) {
+      st = set_err(FA_ERR_NONFINITE, "non-finite convergence measure at iteration %d", k + 1);
+      break;
+    }
+    if (dx < d.tol) {
+      converged = true;
+      break;
+    }
+  }
+  FA_CUDA(cudaMemcpyAsync(dXout, p->U + static_cast<size_t>(d.N) * nn, nn * sizeof(double),
+                          cudaMemcpyDeviceToDevice, p->stream));
+  if (d.refine_steps > 0 && st == FA_OK) {
+    FA_CUDA(cudaEventRecord(ev[1], p->stream));
+    FA_TRY(refine(p, dXout));
+    FA_CUDA(cudaEventRecord(ev[2], p->stream));
+    FA_CUDA(cudaEventSynchronize(ev[2]));
+    FA_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+    t_ref = ms;
+  }
+  fa_status es = read_err(p);
+  if (r) {
+    r->iters = iters;
+    r->converged = converged ? 1 : 0;
+    r->last_dx = dx;
+    r->t_init_ms = t_init;
+    r->t_fine_ms = t_fine;
+    r->t_coarse_ms = t_coarse;
+    r->t_refine_ms = t_ref;
+  }
+  if (es != FA_OK) return es;
+  if (st != FA_OK) return st;
+  if (!converged && d.tol > 0.0)
+    return set_err(FA_ERR_NOT_CONVERGED, "tolerance %.3g not reached in %d iterations (dx %.3g)",
+                   d.tol, iters, dx);
+  return FA_OK;
+}
+
+fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX0, double *hXout,
+                                 fa_report *r) {
+  FA_TRY(check_ready(p, false));
+  if (!hA || !hXout) return set_err(FA_ERR_ARG, "null pointer");
+  const size_t bytes = p->nn * sizeof(double);
+  FA_CUDA(cudaMemcpyAsync(p->A64, hA, bytes, cudaMemcpyHostToDevice, p->stream));
+  if (hX0) FA_CUDA(cudaMemcpyAsync(p->Xin, hX0, bytes, cudaMemcpyHostToDevice, p->stream));
+  fa_status s = fa_parareal_solve(p, p->A64, hX0 ? p->Xin : nullptr, p->Xout, r);
+  if (s != FA_OK && s != FA_ERR_NOT_CONVERGED) return s;
+  FA_CUDA(cudaMemcpyAsync(hXout, p->Xout, bytes, cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaStreamSynchronize(p->stream));
+  return s;
+}
+
+fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, double *dC) {
+  FA_TRY(check_ready(p, false));
+  if (!dL || !dR || !dC) return set_err(FA_ERR_ARG, "null pointer");
+  EpiParams e = base_epi(p);
+  e.mode = fa::EPI_STORE;
+  e.alpha = 1.0;
+  e.beta = 0.0;
+  e.store_out = dC;
+  if (p->cmixed) {
+    const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+    if (!p->Vl[0]) return set_err(FA_ERR_UNSUPPORTED, "debug product needs an L-form buffer (flow inv/sqrt)");
+    FA_CUDA(fa::launch_split_terms(dL, 1, p->d.n, p->ldp, p->Vl[0], tl, p->strideV, nullptr, 0, 0,
+                                   0, p->stream));
+    FA_CUDA(fa::launch_split_terms(dR, 1, p->d.n, p->ldp, nullptr, 0, 0, p->Vr[0], tr, p->strideV,
+                                   0, p->stream));
+    return tc(p, p->tmVl[0], p->tmVr[0], tc_params(p, 1, 0, 0, e));
+  }
+  return f64(p, dL, 0, dR, 0, 1, e);
+}
+
+fa_status fa_plan_destroy(fa_plan_t p) {
+  delete p;
+  return FA_OK;
+}
+
+const char *fa_status_string(fa_status s) {
+  switch (s) {
+    case FA_OK: return "ok";
+    case FA_ERR_ARG: return "invalid argument";
+    case FA_ERR_CUDA: return "CUDA error";
+    case FA_ERR_WORKSPACE: return "workspace missing or too small";
+    case FA_ERR_NONFINITE: return "non-finite values";
+    case FA_ERR_NOT_CONVERGED: return "not converged";
+    case FA_ERR_TIMEOUT: return "device wait timed out";
+    case FA_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *fa_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long fa_launch_count(void) { return g_launches; }
+
+void fa_launch_count_reset(void) { g_launches = 0; }
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal declarations shared by the kernels and the host driver of libfa.
+//
+// Storage conventions inside the workspace (the boundary is always float64
+// row-major):
+//  * parareal state U, G, D: float64 row-major [count][n][n];
+//  * mixed-precision RK4 state (x_hi, x_lo, acc): float32 column-major
+//    [N][n][n] (element (i,j) of slice b at b n^2 + j n + i), so that the
+//    epilogue's thread-per-row mapping gives coalesced warp accesses;
+//  * BF16 operand terms: [term][slice][n][ldp] with ldp = n rounded up to 8
+//    (16-byte rows for TMA).  The "L form" of a matrix Y is row-major
+//    (row i holds Y[i][:]); the "R form" is its transpose (row j holds
+//    Y[:][j]).  A tensor-core product D = L R^T therefore computes
+//    D[i][j] = sum_k L[i][k] R[j][k] = (Y_left * Y_right)[i][j] when the left
+//    factor is given in L form and the right factor in R form.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/fa.h"
+
+namespace fa {
+
+constexpr int kMaxPairs = 6;
+
+enum EpiMode : int {
+  EPI_STAGE = 0,   // RK4 stage combine (fine sweep)
+  EPI_PROD = 1,    // write the product as operand terms (inverse flow: P = (I-A) Y)
+  EPI_EULER = 2,   // forward-Euler substep of G, with the parareal correction on the last one
+  EPI_STORE = 3,   // plain float64 store: out = alpha * v + beta * (i == j)
+};
+
+// Parameters of the fused epilogue.  One struct serves the tensor-core and the
+// float64 kernels; fields that a mode does not use are ignored.
+struct EpiParams {
+  int mode;
+  int flow;
+  int stage;          // 1..4 (EPI_STAGE)
+  int last;           // EPI_STAGE: stage 4 of the slice's last RK4 step -> write F or D
+  int n;
+  int ldp;            // leading dimension of BF16 operand storage
+  int terms_l;        // BF16 terms to write in L form (0 = do not write)
+  int terms_r;        // BF16 terms to write in R form (0 = do not write)
+  size_t term_stride_l, term_stride_r;   // elements between consecutive terms
+  int b0;             // slice offset of this launch inside the state arrays
+  // RK4 coefficients
+  double h;           // fine step
+  double ch;          // c_{s+1} h: Y_{s+1} = X + ch K_s (stages 1..3)
+  // mixed-precision fine state (column-major float32)
+  float *x_hi, *x_lo, *acc;
+  // float64 fine state (row-major)
+  double *x64, *acc64;
+  // the constant matrix for K = A - v (square-root flow)
+  const float *a_hi, *a_lo;     // column-major float32 pair (mixed)
+  const double *a64;            // row-major float64
+  // new operand output (mixed: BF16 terms; f64: row-major float64)
+  __nv_bfloat16 *out_l, *out_r;
+  double *out64;
+  // fine sweep outputs (row-major float64): f_out = X (or X - g_old when g_old != 0)
+  double *f_out;
+  const double *g_old;
+  // EPI_EULER
+  double dt;                    // Euler substep dT/m
+  const double *v_in;           // V (row-major float64) of this substep
+  double *v_out;                // next V (intermediate substep) or V_{n+1} (last substep)
+  double *g_out;                // G_n (last substep)
+  const double *d_in;           // D_n (last substep; 0 = Step 0)
+  const double *u_old;          // previous iterate U_{n+1} for the norms (0 = no norms)
+  double *norm_part;            // per-tile partial sums [tiles][2]
+  int euler_last;               // 1 on the last substep
+  // EPI_STORE
+  double alpha, beta;
+  double *store_out;
+  int *err;                     // device error word
+};
+
+// One tensor-core GEMM launch: for every slice b in [0, nb) and tile,
+// D = sum_p L_{a_p} R_{b_p}^T over the BF16 term pairs, then the epilogue.
+struct TcGemmParams {
+  int n;            // rows of both operands and reduction length
+  int nb;           // slices in this launch
+  int l_batched;    // 1: L has one matrix per slice; 0: shared (slice coordinate 0)
+  int r_batched;
+  int mt, nt;       // tiles per slice along M (128 rows) and N (256 rows)
+  int num_tiles;
+  int kblocks;      // ceil(n / 64)
+  int npairs;
+  int pair_a[kMaxPairs], pair_b[kMaxPairs];
+  uint32_t idesc;   // tcgen05 instruction descriptor
+  EpiParams epi;
+};
+
+// One float64 SIMT GEMM launch: C_b = L_b * R_b (row-major float64), then the epilogue.
+struct F64GemmParams {
+  int n;
+  int nb;
+  const double *L, *R;
+  size_t l_stride, r_stride;     // elements between slices (0 = shared)
+  EpiParams epi;
+};
+
+// Pairs of BF16 terms for each dtype and the number of terms each side needs.
+struct PairSet {
+  int npairs;
+  int a[kMaxPairs], b[kMaxPairs];
+  int terms_l, terms_r;
+};
+PairSet pair_set(int dtype);
+
+// --- launchers (return cudaGetLastError()) ---
+cudaError_t launch_tc_gemm(const CUtensorMap *tmL, const CUtensorMap *tmR,
+                           const TcGemmParams &p, int num_sms, cudaStream_t s);
+cudaError_t launch_f64_gemm(const F64GemmParams &p, cudaStream_t s);
+// Tile edge the float64 GEMM uses for (n, nb), and its tiles per slice.
+int f64_tile(int n, int nb);
+int f64_tiles_per_slice(int n, int nb);
+
+// float64 row-major [nb][n][n] -> BF16 terms (L form and/or R form).  `ident`
+// adds -1 to the diagonal first and negates (to build I - A), when set.
+cudaError_t launch_split_terms(const double *src, int nb, int n, int ldp, __nv_bfloat16 *out_l,
+                               int terms_l, size_t stride_l, __nv_bfloat16 *out_r, int terms_r,
+                               size_t stride_r, int i_minus, cudaStream_t s);
+// float64 row-major [nb][n][n] -> column-major float32 hi/lo pair, plus BF16 terms
+// of hi (the first RK4 stage operand).
+cudaError_t launch_load_state(const double *U, int nb, int n, int ldp, float *x_hi, float *x_lo,
+                              __nv_bfloat16 *out_l, int terms_l, size_t stride_l,
+                              __nv_bfloat16 *out_r, int terms_r, size_t stride_r,
+                              cudaStream_t s);
+// Sum per-tile partial norms in a fixed order: norms[b][2] = sum over tiles.
+cudaError_t launch_reduce_norms(const double *part, int nslices, int tiles_per_slice,
+                                double *norms, cudaStream_t s);
+// dx = max_b sqrt(norms[b][0] / norms[b][1]); flags non-finite values.
+cudaError_t launch_max_ratio(const double *norms, int nslices, double *dx, int *err,
+                             cudaStream_t s);
+// I - A (row-major float64).
+cudaError_t launch_i_minus(const double *A, int n, double *out, cudaStream_t s);
+// Column-major float32 hi/lo copy of A (for K = A - X^2 in the mixed epilogue).
+cudaError_t launch_colmajor_pair(const double *A, int n, float *hi, float *lo, cudaStream_t s);
+// Check an array for non-finite values (sets *err = FA_ERR_NONFINITE).
+cudaError_t launch_check_finite(const double *x, size_t count, int *err, cudaStream_t s);
+// X = I (row-major, count matrices)
+cudaError_t launch_identity(double *X, int n, cudaStream_t s);
+
+// Per-thread launch counter (incremented by every launcher).
+void count_launch();
+
+}  // namespace fa

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of libfa (declared in include/fa.h).
+
+Module-level functions carry the C names and only marshal arguments; every
+step of the computation runs in the library's CUDA kernels.  `Plan` is a
+convenience wrapper that allocates the workspace with PyTorch (the library
+itself never allocates device memory) and passes raw device pointers and the
+stream handle.  If the library has not been built, every call raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfa.so")
+
+FA_OK = 0
+FA_ERR_NOT_CONVERGED = 5
+FA_FLOW_INV, FA_FLOW_EXP, FA_FLOW_SQRT = 0, 1, 2
+FA_F64, FA_BF16, FA_BF16X3, FA_BF16X4, FA_BF16X6 = 0, 1, 2, 3, 4
+DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16X4,
+          "bf16x6": FA_BF16X6}
+SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_sweep",
+           "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
+           "fa_debug_product", "fa_plan_destroy", "fa_status_string", "fa_last_error",
+           "fa_launch_count", "fa_launch_count_reset"]
+
+
+class fa_problem_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("flow", ctypes.c_int), ("T", ctypes.c_double),
+                ("N", ctypes.c_int), ("coarse_steps", ctypes.c_int), ("fine_steps", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
+                ("fine_dtype", ctypes.c_int), ("coarse_dtype", ctypes.c_int),
+                ("refine_steps", ctypes.c_int)]
+
+
+class fa_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_dx", ctypes.c_double),
+                ("t_init_ms", ctypes.c_double), ("t_fine_ms", ctypes.c_double),
+                ("t_coarse_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double),
+                ("dx_history", ctypes.POINTER(ctypes.c_double))]
+
+
+class FaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libfa status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfa.so and declare the C signatures (raises if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1505_07959_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    vp, sz, dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+    sigs = {
+        "fa_plan": [ctypes.POINTER(vp), ctypes.POINTER(fa_problem_desc), vp, ctypes.POINTER(sz)],
+        "fa_plan_bind_workspace": [vp, vp, sz],
+        "fa_plan_set_matrix": [vp, dp],
+        "fa_fine_sweep": [vp, dp, dp],
+        "fa_coarse_sweep": [vp, dp, dp, dp, dp, dp, dp],
+        "fa_refine": [vp, dp],
+        "fa_parareal_solve": [vp, dp, dp, dp, ctypes.POINTER(fa_report)],
+        "fa_parareal_solve_host": [vp, dp, dp, dp, ctypes.POINTER(fa_report)],
+        "fa_debug_product": [vp, dp, dp, dp],
+        "fa_plan_destroy": [vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fa_status_string.argtypes = [ctypes.c_int]
+    lib.fa_status_string.restype = ctypes.c_char_p
+    lib.fa_last_error.argtypes = []
+    lib.fa_last_error.restype = ctypes.c_char_p
+    lib.fa_launch_count.argtypes = []
+    lib.fa_launch_count.restype = ctypes.c_ulonglong
+    lib.fa_launch_count_reset.argtypes = []
+    lib.fa_launch_count_reset.restype = None
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, allow=(FA_OK,)) -> int:
+    if status not in allow:
+        lib = load_library()
+        raise FaError(status, lib.fa_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# --- the C names ----------------------------------------------------------------------------
+
+def fa_plan(desc: fa_problem_desc, stream_handle: int):
+    lib = load_library()
+    h, ws = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(lib.fa_plan(ctypes.byref(h), ctypes.byref(desc), ctypes.c_void_p(stream_handle),
+                       ctypes.byref(ws)))
+    return h, ws.value
+
+
+def fa_plan_bind_workspace(h, ws_ptr: int, nbytes: int):
+    _check(load_library().fa_plan_bind_workspace(h, ctypes.c_void_p(ws_ptr), nbytes))
+
+
+def fa_plan_set_matrix(h, dA):
+    _check(load_library().fa_plan_set_matrix(h, _ptr(dA)))
+
+
+def fa_fine_sweep(h, dU, dF):
+    _check(load_library().fa_fine_sweep(h, _ptr(dU), _ptr(dF)))
+
+
+def fa_coarse_sweep(h, dU0, dD, dUnew, dGnew, dNorms, dUold):
+    _check(load_library().fa_coarse_sweep(h, _ptr(dU0), _ptr(dD), _ptr(dUnew), _ptr(dGnew),
+                                          _ptr(dNorms), _ptr(dUold)))
+
+
+def fa_refine(h, dX):
+    _check(load_library().fa_refine(h, _ptr(dX)))
+
+
+def fa_parareal_solve(h, dA, dX0, dXout, report: fa_report):
+    return _check(load_library().fa_parareal_solve(h, _ptr(dA), _ptr(dX0), _ptr(dXout),
+                                                   ctypes.byref(report)),
+                  allow=(FA_OK, FA_ERR_NOT_CONVERGED))
+
+
+def fa_parareal_solve_host(h, hA: np.ndarray, hX0, hXout: np.ndarray, report: fa_report):
+    dp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    return _check(load_library().fa_parareal_solve_host(h, dp(hA), dp(hX0), dp(hXout),
+                                                        ctypes.byref(report)),
+                  allow=(FA_OK, FA_ERR_NOT_CONVERGED))
+
+
+def fa_debug_product(h, dL, dR, dC):
+    _check(load_library().fa_debug_product(h, _ptr(dL), _ptr(dR), _ptr(dC)))
+
+
+def fa_plan_destroy(h):
+    if _LIB is not None and h:
+        _LIB.fa_plan_destroy(h)
+
+
+def fa_status_string(status: int) -> str:
+    return load_library().fa_status_string(status).decode()
+
+
+def fa_last_error() -> str:
+    return load_library().fa_last_error().decode()
+
+
+def fa_launch_count() -> int:
+    return int(load_library().fa_launch_count())
+
+
+def fa_launch_count_reset() -> None:
+    load_library().fa_launch_count_reset()
+
+
+# --- convenience wrapper ----------------------------------------------------------------------
+
+class Plan:
+    """A plan plus its PyTorch-allocated workspace, on the current CUDA stream."""
+
+    def __init__(self, n, flow, T, N, fine_steps, coarse_steps=1, max_iters=None, tol=0.0,
+                 fine_dtype="f64", coarse_dtype=None, refine_steps=0, stream=None):
+        import torch
+
+        self.torch = torch
+        fd = DTYPES[fine_dtype] if isinstance(fine_dtype, str) else int(fine_dtype)
+        cd = fd if coarse_dtype is None else (DTYPES[coarse_dtype] if isinstance(coarse_dtype, str)
+                                              else int(coarse_dtype))
+        self.desc = fa_problem_desc(n=n, flow=flow, T=float(T), N=N, coarse_steps=coarse_steps,
+                                    fine_steps=fine_steps,
+                                    max_iters=N if max_iters is None else max_iters,
+                                    tol=float(tol), fine_dtype=fd, coarse_dtype=cd,
+                                    refine_steps=refine_steps)
+        self.n, self.N = n, N
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle, self.ws_bytes = fa_plan(self.desc, self.stream.cuda_stream)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
+        fa_plan_bind_workspace(self.handle, self.ws.data_ptr(), self.ws_bytes)
+
+    def _f64(self, x, shape):
+        t = self.torch.as_tensor(x, dtype=self.torch.float64)
+        if t.device.type != "cuda":
+            t = t.cuda()
+        t = t.contiguous()
+        assert tuple(t.shape) == tuple(shape), (tuple(t.shape), shape)
+        return t
+
+    def set_matrix(self, A):
+        self.A = self._f64(A, (self.n, self.n))
+        fa_plan_set_matrix(self.handle, self.A)
+
+    def fine_sweep(self, U):
+        U = self._f64(U, (self.N, self.n, self.n))
+        F = self.torch.empty_like(U)
+        fa_fine_sweep(self.handle, U, F)
+        return F
+
+    def coarse_sweep(self, U0, D=None, Uold=None):
+        n, N = self.n, self.N
+        U0 = self._f64(U0, (n, n))
+        D = None if D is None else self._f64(D, (N, n, n))
+        Unew = self.torch.empty((N + 1, n, n), dtype=self.torch.float64, device="cuda")
+        Gnew = self.torch.empty((N, n, n), dtype=self.torch.float64, device="cuda")
+        norms = None
+        if Uold is not None:
+            Uold = self._f64(Uold, (N + 1, n, n))
+            norms = self.torch.empty((N, 2), dtype=self.torch.float64, device="cuda")
+        fa_coarse_sweep(self.handle, U0, D, Unew, Gnew, norms, Uold)
+        return Unew, Gnew, norms
+
+    def refine(self, X):
+        X = self._f64(X, (self.n, self.n)).clone()
+        fa_refine(self.handle, X)
+        return X
+
+    def debug_product(self, L, R):
+        L = self._f64(L, (self.n, self.n))
+        R = self._f64(R, (self.n, self.n))
+        C = self.torch.empty_like(L)
+        fa_debug_product(self.handle, L, R, C)
+        return C
+
+    def solve(self, A, X0=None, out=None):
+        """Returns (X, report dict).  Not converging within max_iters is reported, not raised."""
+        A = self._f64(A, (self.n, self.n))
+        X0 = None if X0 is None else self._f64(X0, (self.n, self.n))
+        X = out if out is not None else self.torch.empty_like(A)
+        hist = (ctypes.c_double * max(self.desc.max_iters, 1))()
+        rep = fa_report()
+        rep.dx_history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        st = fa_parareal_solve(self.handle, A, X0, X, rep)
+        return X, _report(rep, hist, st)
+
+    def solve_host(self, A: np.ndarray, X0=None, out=None):
+        """The same solve on host arrays (float64, C-contiguous); copies happen inside the call."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        X0 = None if X0 is None else np.ascontiguousarray(X0, dtype=np.float64)
+        X = out if out is not None else np.empty_like(A)
+        hist = (ctypes.c_double * max(self.desc.max_iters, 1))()
+        rep = fa_report()
+        rep.dx_history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        st = fa_parareal_solve_host(self.handle, A, X0, X, rep)
+        return X, _report(rep, hist, st)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _report(rep: fa_report, hist, status) -> dict:
+    return {"iters": rep.iters, "converged": bool(rep.converged), "last_dx": rep.last_dx,
+            "dx_history": [hist[i] for i in range(rep.iters)], "t_init_ms": rep.t_init_ms,
+            "t_fine_ms": rep.t_fine_ms, "t_coarse_ms": rep.t_coarse_ms,
+            "t_refine_ms": rep.t_refine_ms, "status": status}
