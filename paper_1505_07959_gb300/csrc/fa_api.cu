@@ -123,7 +123,7 @@ struct fa_plan_s {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256;
+constexpr int TC_BM = 128, TC_BN = 128;
 
 size_t carve(fa_plan_s *p, char *base) {
   Carver c{base};

@@ -9,7 +9,10 @@ from paper_1505_07959_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FLOWS = [(fa.FA_FLOW_INV, "inv", 1.0), (fa.FA_FLOW_EXP, "exp", 1.0), (fa.FA_FLOW_SQRT, "sqrt", 4.0)]
+# Horizons keep one Euler substep per slice stable for every flow (for the square-root flow
+# dT = 1 keeps the coarse iterates positive definite; with dT = 2, I + 2(A - I) has negative
+# eigenvalues and the flow X' = A - X^2 blows up from there, in the oracle as well).
+FLOWS = [(fa.FA_FLOW_INV, "inv", 1.0), (fa.FA_FLOW_EXP, "exp", 1.0), (fa.FA_FLOW_SQRT, "sqrt", 2.0)]
 # Error of the mixed fine sweep relative to ||F||_F: J steps of size h each add
 # h ||Fl'|| times the product error of the dtype; over one slice (J h = dT) and
 # with ||Fl'|| <= 4 on these spectra that is ~4 dT eps_d, plus the float32
@@ -77,7 +80,10 @@ def test_coarse_sweep(m, dtype, flow, kind, T):
     # Step 0 (no correction)
     U0g, G0g, _ = plan.coarse_sweep(dev(np.eye(n)))
     U0, G0 = orc.coarse_sweep(sm.A, flow, T, N, m, np.eye(n))
-    tol = 1e-13 if dtype == "f64" else 1e-7
+    # float64: summation order only.  Mixed: each product element is rounded to float32
+    # (2^-24) before the float64 Euler update, so G carries ~dt 2^-24 relative error per
+    # substep; over N*m <= 15 substeps with dt ||Fl'|| <= 1 that stays below 1e-6.
+    tol = 1e-13 if dtype == "f64" else 1e-6
     for k in range(N + 1):
         assert rel(host(U0g)[k], U0[k]) < tol
     for k in range(N):

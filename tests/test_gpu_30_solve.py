@@ -60,6 +60,14 @@ def test_finite_termination_f64(flow, kind, T, m):
     assert rel(host(X), seq) < 1e-12
 
 
+# Relative error of a mixed solve vs the oracle.  BF16X6 keeps both operands to float32
+# precision and drains the main product every k-block, so the solve stays near the
+# float32 level (bound 1e-6).  BF16X4 keeps the right operand to two BF16 terms
+# (~2^-18 = 3.8e-6 per element); over T ||Fl'|| <= 8 (square root, T = 8) that allows
+# up to ~3e-5, bound 1e-5 on these inputs.
+SOLVE_TOL = {"bf16x4": 1e-5, "bf16x6": 1e-6}
+
+
 @pytest.mark.parametrize("dtype", ["bf16x4", "bf16x6"])
 @pytest.mark.parametrize("flow,kind,T,m", FLOWS)
 def test_solve_mixed(dtype, flow, kind, T, m):
@@ -71,7 +79,7 @@ def test_solve_mixed(dtype, flow, kind, T, m):
     X, rep = plan.solve(dev(sm.A))
     e = rel(host(X), ref.U[N])
     print(f"solve {dtype} flow={kind}: iters {rep['iters']} (oracle {ref.iterations}) err {e:.2e}")
-    assert e < 1e-6
+    assert e < SOLVE_TOL[dtype]
     assert abs(rep["iters"] - ref.iterations) <= 1
 
 
