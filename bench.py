@@ -224,9 +224,9 @@ def run_ours(args):
     value = ws * args.steps / t
 
     # accuracy of the last solve against exp(A) from a float64 eigendecomposition (outside timing)
-    w, V = torch.linalg.eigh(A)
-    ref = (V * torch.exp(w)) @ V.T
-    rel_err = float(torch.linalg.norm(X - ref) / torch.linalg.norm(ref))
+    w, V = np.linalg.eigh(sm.A)
+    ref = (V * np.exp(w)) @ V.T
+    rel_err = float(np.linalg.norm(X.cpu().numpy() - ref) / np.linalg.norm(ref))
 
     # --- end to end through the host-buffer entry point (pinned host memory) ---
     hA = torch.from_numpy(sm.A).pin_memory()

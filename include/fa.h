@@ -172,6 +172,16 @@ fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX
  * buffer (FA_FLOW_INV or FA_FLOW_SQRT); FA_ERR_UNSUPPORTED otherwise. */
 fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, double *dC);
 
+/* Diagnostic: when d_counters (device, >= 16 unsigned 64-bit words, zeroed by the
+ * caller) is not NULL, later tensor-core launches add per-role cycle counts to it:
+ * [0] producer waiting for free slots, [1] MMA waiting for operand tiles, [2] MMA
+ * waiting for a free main chunk, [3] MMA waiting for the correction buffer,
+ * [4] drain waiting for a main chunk, [5] drain waiting for corrections, [6] drain
+ * waiting for the finished-tile buffer, [7] epilogue waiting for a finished tile,
+ * [8] epilogue busy, [9] drain busy, [10] kernel cycles per CTA, [11] tiles.
+ * NULL switches it off. */
+fa_status fa_debug_set_profile(unsigned long long *d_counters);
+
 /* Release the plan (not the workspace, which the caller owns). */
 fa_status fa_plan_destroy(fa_plan_t p);
 

@@ -17,6 +17,7 @@ using fa::TcGemmParams;
 namespace {
 
 thread_local std::string g_last_error;
+unsigned long long *g_prof = nullptr;   // diagnostics: per-role cycle counters of the TC kernel
 thread_local unsigned long long g_launches = 0;
 
 fa_status set_err(fa_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -249,11 +250,8 @@ TcGemmParams tc_params(const fa_plan_s *p, int nb, int l_batched, int r_batched,
   g.nt = (p->d.n + TC_BN - 1) / TC_BN;
   g.num_tiles = g.mt * g.nt * nb;
   g.kblocks = (p->d.n + 63) / 64;
-  g.npairs = p->ps.npairs;
-  for (int k = 0; k < g.npairs; ++k) {
-    g.pair_a[k] = p->ps.a[k];
-    g.pair_b[k] = p->ps.b[k];
-  }
+  fa::tc_schedule(p->ps, g);
+  g.prof = g_prof;
   g.idesc = fa::ptx::idesc_bf16_f32(TC_BM, TC_BN);
   g.epi = e;
   return g;
@@ -713,6 +711,11 @@ fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, doub
     return tc(p, p->tmVl[0], p->tmVr[0], tc_params(p, 1, 0, 0, e));
   }
   return f64(p, dL, 0, dR, 0, 1, e);
+}
+
+fa_status fa_debug_set_profile(unsigned long long *d_counters) {
+  g_prof = d_counters;
+  return FA_OK;
 }
 
 fa_status fa_plan_destroy(fa_plan_t p) {

@@ -80,17 +80,24 @@ struct EpiParams {
 
 // One tensor-core GEMM launch: for every slice b in [0, nb) and tile,
 // D = sum_p L_{a_p} R_{b_p}^T over the BF16 term pairs, then the epilogue.
+// Each 64-wide k-block loads its operand term tiles once (tl_side / tl_term,
+// in load order) and issues pair p once tile pair_at[p] has landed; pair 0 is
+// the main product L_0 R_0^T.
 struct TcGemmParams {
   int n;            // rows of both operands and reduction length
   int nb;           // slices in this launch
   int l_batched;    // 1: L has one matrix per slice; 0: shared (slice coordinate 0)
   int r_batched;
-  int mt, nt;       // tiles per slice along M (128 rows) and N (256 rows)
+  int mt, nt;       // tiles per slice along M and N (128 rows each)
   int num_tiles;
   int kblocks;      // ceil(n / 64)
+  int ntl;          // operand tiles per k-block
+  int tl_side[2 * 3];   // 0 = left operand (L form), 1 = right operand (R form)
+  int tl_term[2 * 3];
   int npairs;
-  int pair_a[kMaxPairs], pair_b[kMaxPairs];
+  int pair_tl[kMaxPairs], pair_tr[kMaxPairs], pair_at[kMaxPairs];
   uint32_t idesc;   // tcgen05 instruction descriptor
+  unsigned long long *prof;   // optional per-role cycle counters (diagnostics), may be null
   EpiParams epi;
 };
 
@@ -110,6 +117,8 @@ struct PairSet {
   int terms_l, terms_r;
 };
 PairSet pair_set(int dtype);
+// Fill the tile list and pair schedule of a launch from a pair set.
+void tc_schedule(const PairSet &ps, TcGemmParams &g);
 
 // --- launchers (return cudaGetLastError()) ---
 cudaError_t launch_tc_gemm(const CUtensorMap *tmL, const CUtensorMap *tmR,

@@ -16,11 +16,21 @@
 // products (2^-8 smaller, so their bias is negligible) accumulate in a second
 // TMEM buffer for the whole tile.
 //
-// Roles (one CTA per SM, 10 warps): warp 0 issues TMA loads into a 4-stage
-// shared-memory ring; warp 1 issues tcgen05.mma; warps 2-5 drain TMEM into
-// registers and hand the finished 128 x 128 tile to warps 6-9 through shared
-// memory; warps 6-9 run the epilogue (global memory) while the next tile's
-// MMAs proceed.  Tiles are scheduled persistently, M-tile fastest.
+// Data movement.  Each k-block's operand term tiles (16 KB each) are loaded
+// once by TMA into a 13-slot shared-memory ring and every term pair that uses
+// them is issued from there, so about two k-blocks are in flight.
+//
+// Roles (one CTA per SM, 10 warps): warp 0 issues TMA loads; warp 1 issues
+// tcgen05.mma; warps 2-5 drain each main chunk into a float32 running sum in
+// registers (round-to-nearest adds), add the corrections at the end of the
+// tile and store the finished tile into TMEM; warps 6-9 read it from TMEM
+// (one row per thread) and run the epilogue against global memory.  The
+// finished-tile buffer is written only at the end of the next tile, so the
+// epilogue of tile t overlaps all of tile t+1's MMAs.  Tiles are scheduled
+// persistently, M-tile fastest.
+//
+// TMEM columns: [0,128) and [128,256) main-product chunks (double-buffered),
+// [256,384) correction accumulator, [384,512) finished tile.
 #include <cuda_bf16.h>
 
 #include "fa_internal.h"
@@ -33,17 +43,16 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;
-constexpr int STAGES = 4;
-constexpr int L_BYTES = BM * BK * 2;
-constexpr int R_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = L_BYTES + R_BYTES;
-constexpr int KS_LD = BM + 1;                 // hand-off tile: column-major, padded
-constexpr int KS_BYTES = BN * KS_LD * 4;
-constexpr int THREADS = 320;
+constexpr int NSLOT = 13;
+constexpr int NKB = 8;                        // k-block release barriers (> k-blocks in flight)
+constexpr int TILE_BYTES = BM * BK * 2;       // one operand term tile: 128 rows x 64 BF16
+constexpr int STORE_WARPS = 4;                // one per TMEM lane quarter
+constexpr int THREADS = (6 + STORE_WARPS) * 32;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t MB_COL0 = 0;               // main-product chunks: columns [0,128), [128,256)
-constexpr uint32_t CB_COL0 = 256;             // correction accumulators: [256,384), [384,512)
-constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + KS_BYTES + 1024 + 512;
+constexpr uint32_t MB_COL0 = 0;               // main-product chunks: [0,128) and [128,256)
+constexpr uint32_t CB_COL = 256;
+constexpr uint32_t FIN_COL = 384;
+constexpr size_t SMEM_BYTES = size_t(NSLOT) * TILE_BYTES + 1024 + 512;
 
 __device__ __forceinline__ void split_f32(float x, int nt, __nv_bfloat16 *t) {
   float r = x;
@@ -69,188 +78,232 @@ __device__ __forceinline__ void split_f64(double x, int nt, __nv_bfloat16 *t) {
   }
 }
 
-__device__ __forceinline__ void put_r(const EpiParams &e, int b, int i, int j,
-                                      const __nv_bfloat16 *t) {
-  const size_t off = (static_cast<size_t>(b) * e.n + j) * e.ldp + i;
-  for (int k = 0; k < e.terms_r; ++k) e.out_r[k * e.term_stride_r + off] = t[k];
+__device__ __forceinline__ int nterms(const EpiParams &e) {
+  return e.terms_l > e.terms_r ? e.terms_l : e.terms_r;
 }
 
-__device__ __forceinline__ void put_l(const EpiParams &e, int b, int i, int j,
-                                      const __nv_bfloat16 *t) {
-  const size_t off = (static_cast<size_t>(b) * e.n + i) * e.ldp + j;
-  for (int k = 0; k < e.terms_l; ++k) e.out_l[k * e.term_stride_l + off] = t[k];
-}
-
-// RK4 stage combine for element (i, j) of slice b with K = Fl(Y_s)_{ij} (low-storage
-// form: acc = K1 + 2K2 + 2K3, Y_{s+1} = X + c_{s+1} h K_s, X <- X + h/6 (acc + K4),
-// X kept as an unevaluated float32 sum hi + lo).  Returns the next stage operand
-// Y_{s+1}; writes its R-form terms.  On the last step writes F (or F - G_old).
-__device__ __forceinline__ float stage_elem(const EpiParams &e, int b, int i, int j, float v) {
-  const int n = e.n;
-  const size_t nn = static_cast<size_t>(n) * n;
-  const size_t c = static_cast<size_t>(j) * n + i;
-  float *xh = e.x_hi + b * nn;
-  float *xl = e.x_lo + b * nn;
-  float *ac = e.acc + b * nn;
-  float K = v;
-  if (e.flow == FA_FLOW_SQRT) K = (e.a_hi[c] - K) + e.a_lo[c];
-  const float ch = static_cast<float>(e.ch);
-  float y;
-  if (e.stage == 1) {
-    ac[c] = K;
-    y = xh[c] + ch * K;
-  } else if (e.stage < 4) {
-    ac[c] = ac[c] + 2.0f * K;
-    y = xh[c] + ch * K;
-  } else {
-    const float inc = static_cast<float>(e.h / 6.0) * (ac[c] + K);
-    const float a = xh[c];
-    const float s = a + inc;
-    const float bp = s - a;
-    const float er = (a - (s - bp)) + (inc - bp);   // two-sum error of a + inc
-    float lo = xl[c] + er;
-    const float hi = s + lo;
-    lo = lo - (hi - s);
-    xh[c] = hi;
-    xl[c] = lo;
-    y = hi;
-    if (e.last) {
-      const double X = static_cast<double>(hi) + static_cast<double>(lo);
-      const size_t r = b * nn + static_cast<size_t>(i) * n + j;
-      e.f_out[r] = e.g_old ? X - e.g_old[r] : X;
-    }
-  }
-  if (!e.last && e.terms_r) {
-    __nv_bfloat16 t[3];
-    split_f32(y, e.terms_r > e.terms_l ? e.terms_r : e.terms_l, t);
-    put_r(e, b, i, j, t);
-  }
-  return y;
-}
-
-// The same stage combine for four consecutive rows i0..i0+3 of column j (i0 % 4 == 0,
-// n % 4 == 0): 16-byte loads/stores of the column-major state and 8-byte stores of the
-// R-form terms.  v[u] is the product value of row i0 + u; on return y[u] holds Y_{s+1}.
-struct Quad {
-  float4 xh, xl, ac, ah, al;
+// Operand terms of a value, held in scalars (no runtime-indexed arrays).
+struct Terms3 {
+  __nv_bfloat16 t0, t1, t2;
 };
 
-__device__ __forceinline__ void stage_quad_load(const EpiParams &e, size_t c, Quad &q) {
-  q.xh = *reinterpret_cast<const float4 *>(e.x_hi + c);
-  if (e.stage > 1) q.ac = *reinterpret_cast<const float4 *>(e.acc + c);
-  if (e.stage == 4) q.xl = *reinterpret_cast<const float4 *>(e.x_lo + c);
+__device__ __forceinline__ Terms3 split3_f32(float x) {
+  Terms3 r;
+  r.t0 = __float2bfloat16_rn(x);
+  float rem = x - __bfloat162float(r.t0);
+  r.t1 = __float2bfloat16_rn(rem);
+  rem -= __bfloat162float(r.t1);
+  r.t2 = __float2bfloat16_rn(rem);
+  return r;
 }
 
-__device__ __forceinline__ void stage_quad_finish(const EpiParams &e, int b, int i0, int j,
-                                                  size_t c, const float (&v)[4], Quad &q,
-                                                  float (&y)[4]) {
-  const int n = e.n;
-  float K[4] = {v[0], v[1], v[2], v[3]};
-  if (e.flow == FA_FLOW_SQRT) {
-    const size_t ca = static_cast<size_t>(j) * n + i0;
-    const float4 ah = *reinterpret_cast<const float4 *>(e.a_hi + ca);
-    const float4 al = *reinterpret_cast<const float4 *>(e.a_lo + ca);
-    K[0] = (ah.x - K[0]) + al.x;
-    K[1] = (ah.y - K[1]) + al.y;
-    K[2] = (ah.z - K[2]) + al.z;
-    K[3] = (ah.w - K[3]) + al.w;
+__device__ __forceinline__ Terms3 split3_f64(double x) {
+  Terms3 r;
+  r.t0 = __double2bfloat16(x);
+  double rem = x - static_cast<double>(__bfloat162float(r.t0));
+  r.t1 = __double2bfloat16(rem);
+  rem -= static_cast<double>(__bfloat162float(r.t1));
+  r.t2 = __double2bfloat16(rem);
+  return r;
+}
+
+// R form of element (i, j): transposed storage, coalesced across a warp's rows.
+__device__ __forceinline__ void put_r(const EpiParams &e, int b, int i, int j, const Terms3 &t) {
+  __nv_bfloat16 *o = e.out_r + (static_cast<size_t>(b) * e.n + j) * e.ldp + i;
+  o[0] = t.t0;
+  if (e.terms_r > 1) o[e.term_stride_r] = t.t1;
+  if (e.terms_r > 2) o[2 * e.term_stride_r] = t.t2;
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(a)) |
+         (static_cast<uint32_t>(__bfloat16_as_ushort(b)) << 16);
+}
+
+// L form of 8 consecutive columns (one 16-byte store per term).
+__device__ __forceinline__ void put_l8(const EpiParams &e, size_t off, const Terms3 (&t)[8]) {
+  uint4 w;
+  w.x = pack2(t[0].t0, t[1].t0); w.y = pack2(t[2].t0, t[3].t0);
+  w.z = pack2(t[4].t0, t[5].t0); w.w = pack2(t[6].t0, t[7].t0);
+  *reinterpret_cast<uint4 *>(e.out_l + off) = w;
+  if (e.terms_l > 1) {
+    w.x = pack2(t[0].t1, t[1].t1); w.y = pack2(t[2].t1, t[3].t1);
+    w.z = pack2(t[4].t1, t[5].t1); w.w = pack2(t[6].t1, t[7].t1);
+    *reinterpret_cast<uint4 *>(e.out_l + e.term_stride_l + off) = w;
   }
-  float xh[4] = {q.xh.x, q.xh.y, q.xh.z, q.xh.w};
+  if (e.terms_l > 2) {
+    w.x = pack2(t[0].t2, t[1].t2); w.y = pack2(t[2].t2, t[3].t2);
+    w.z = pack2(t[4].t2, t[5].t2); w.w = pack2(t[6].t2, t[7].t2);
+    *reinterpret_cast<uint4 *>(e.out_l + 2 * e.term_stride_l + off) = w;
+  }
+}
+
+__device__ __forceinline__ void put_l1(const EpiParams &e, size_t off, const Terms3 &t) {
+  e.out_l[off] = t.t0;
+  if (e.terms_l > 1) e.out_l[e.term_stride_l + off] = t.t1;
+  if (e.terms_l > 2) e.out_l[2 * e.term_stride_l + off] = t.t2;
+}
+
+// RK4 stage combine on 32 columns j0.. of row i of slice b, with v = the product
+// (low-storage form: acc = K1 + 2K2 + 2K3, Y_{s+1} = X + c_{s+1} h K_s,
+// X <- X + h/6 (acc + K4), X kept as an unevaluated float32 sum hi + lo).
+// Writes the next stage operand Y_{s+1} in R and L form; on the slice's last step
+// writes F (or F - G_old) in float64 row-major instead.  Columns go in groups of
+// 16 whose state loads are issued before any of them is used.
+template <int STAGE, bool SQRT, bool LAST>
+__device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, int j0, int cnt,
+                                            const float (&v)[32]) {
+  constexpr int GW = 16;
+  const int n = e.n;
+  const size_t nn = static_cast<size_t>(n) * n;
+  const size_t base = b * nn + static_cast<size_t>(j0) * n + i;   // column-major (i, j0)
   const float ch = static_cast<float>(e.ch);
-  if (e.stage == 1) {
-    *reinterpret_cast<float4 *>(e.acc + c) = make_float4(K[0], K[1], K[2], K[3]);
+  const float h6 = static_cast<float>(e.h / 6.0);
+  float *__restrict__ xhp = e.x_hi;
+  float *__restrict__ xlp = e.x_lo;
+  float *__restrict__ acp = e.acc;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) y[u] = xh[u] + ch * K[u];
-  } else if (e.stage < 4) {
-    float ac[4] = {q.ac.x, q.ac.y, q.ac.z, q.ac.w};
+  for (int g = 0; g < 32 / GW; ++g) {
+    const int gcnt = cnt - GW * g;
+    if (gcnt <= 0) break;
+    float xh[GW], ac[GW], xl[GW], K[GW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      ac[u] = ac[u] + 2.0f * K[u];
-      y[u] = xh[u] + ch * K[u];
+    for (int u = 0; u < GW; ++u) {
+      const size_t c = base + static_cast<size_t>(GW * g + u) * n;
+      const bool ok = u < gcnt;
+      xh[u] = ok ? xhp[c] : 0.0f;
+      if (STAGE > 1) ac[u] = ok ? acp[c] : 0.0f;
+      if (STAGE == 4) xl[u] = ok ? xlp[c] : 0.0f;
+      K[u] = v[GW * g + u];
+      if (SQRT && ok) {
+        const size_t ca = static_cast<size_t>(j0 + GW * g + u) * n + i;
+        K[u] = (e.a_hi[ca] - K[u]) + e.a_lo[ca];
+      }
     }
-    *reinterpret_cast<float4 *>(e.acc + c) = make_float4(ac[0], ac[1], ac[2], ac[3]);
-  } else {
-    const float ac[4] = {q.ac.x, q.ac.y, q.ac.z, q.ac.w};
-    float xl[4] = {q.xl.x, q.xl.y, q.xl.z, q.xl.w};
-    const float h6 = static_cast<float>(e.h / 6.0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float inc = h6 * (ac[u] + K[u]);
-      const float a = xh[u];
-      const float s = a + inc;
-      const float bp = s - a;
-      const float er = (a - (s - bp)) + (inc - bp);
-      float lo = xl[u] + er;
-      const float hi = s + lo;
-      lo = lo - (hi - s);
-      xh[u] = hi;
-      xl[u] = lo;
-      y[u] = hi;
+    for (int u = 0; u < GW; ++u) {
+      if (u >= gcnt) continue;
+      const size_t c = base + static_cast<size_t>(GW * g + u) * n;
+      if (STAGE == 1) {
+        acp[c] = K[u];
+        xh[u] = xh[u] + ch * K[u];          // Y_2
+      } else if (STAGE < 4) {
+        acp[c] = ac[u] + 2.0f * K[u];
+        xh[u] = xh[u] + ch * K[u];          // Y_3 or Y_4
+      } else {
+        const float inc = h6 * (ac[u] + K[u]);
+        const float a = xh[u];
+        const float s = a + inc;
+        const float bp = s - a;
+        const float er = (a - (s - bp)) + (inc - bp);   // two-sum error of a + inc
+        float lo = xl[u] + er;
+        const float hi = s + lo;
+        lo = lo - (hi - s);
+        xhp[c] = hi;
+        xlp[c] = lo;
+        xh[u] = hi;                         // Y_1 of the next step
+        xl[u] = lo;
+      }
     }
-    *reinterpret_cast<float4 *>(e.x_hi + c) = make_float4(xh[0], xh[1], xh[2], xh[3]);
-    *reinterpret_cast<float4 *>(e.x_lo + c) = make_float4(xl[0], xl[1], xl[2], xl[3]);
-    if (e.last) {
-      const size_t nn = static_cast<size_t>(n) * n;
+    if (LAST) {
+      const size_t r0 = b * nn + static_cast<size_t>(i) * n + j0 + GW * g;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const double X = static_cast<double>(xh[u]) + static_cast<double>(xl[u]);
-        const size_t r = b * nn + static_cast<size_t>(i0 + u) * n + j;
-        e.f_out[r] = e.g_old ? X - e.g_old[r] : X;
+      for (int u = 0; u < GW; ++u) {
+        if (u < gcnt) {
+          const double X = static_cast<double>(xh[u]) + static_cast<double>(xl[u]);
+          e.f_out[r0 + u] = e.g_old ? X - e.g_old[r0 + u] : X;
+        }
+      }
+      continue;
+    }
+#pragma unroll
+    for (int h8 = 0; h8 < GW / 8; ++h8) {
+      Terms3 t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = split3_f32(xh[8 * h8 + u]);
+      if (e.terms_r) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (8 * h8 + u < gcnt) put_r(e, b, i, j0 + GW * g + 8 * h8 + u, t[u]);
+      }
+      if (e.terms_l) {
+        const size_t off = (static_cast<size_t>(b) * n + i) * e.ldp + j0 + GW * g + 8 * h8;
+        if (8 * h8 + 8 <= gcnt) {
+          put_l8(e, off, t);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (8 * h8 + u < gcnt) put_l1(e, off + u, t[u]);
+        }
       }
     }
   }
 }
 
-// BF16 terms of four consecutive rows i0..i0+3 of column j, R form (8-byte stores).
-__device__ __forceinline__ void put_r_quad(const EpiParams &e, int b, int i0, int j,
-                                           const float (&y)[4], int nt) {
-  __nv_bfloat16 t[4][3];
+// Forward-Euler substep G = V + dt Fl(V) on 32 columns of row i (single slice,
+// row-major float64); on the last substep also G_n, the correction
+// V_{n+1} = G_n + D_n and the norm terms.  Writes V's operand terms.
+__device__ __forceinline__ void euler_chunk(const EpiParams &e, int i, int j0, int cnt,
+                                            const float (&v)[32], double &s0, double &s1) {
+  const int n = e.n;
+  const size_t r0 = static_cast<size_t>(i) * n + j0;
+  double Vn[32];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) split_f32(y[u], nt, t[u]);
-  const size_t off = (static_cast<size_t>(b) * e.n + j) * e.ldp + i0;
-  for (int k = 0; k < e.terms_r; ++k) {
-    __nv_bfloat162 lo2, hi2;
-    lo2.x = t[0][k];
-    lo2.y = t[1][k];
-    hi2.x = t[2][k];
-    hi2.y = t[3][k];
-    uint2 w;
-    w.x = *reinterpret_cast<uint32_t *>(&lo2);
-    w.y = *reinterpret_cast<uint32_t *>(&hi2);
-    *reinterpret_cast<uint2 *>(e.out_r + k * e.term_stride_r + off) = w;
+  for (int jj = 0; jj < 32; ++jj) {
+    Vn[jj] = 0.0;
+    if (jj < cnt) {
+      double K = static_cast<double>(v[jj]);
+      if (e.flow == FA_FLOW_SQRT) {
+        const size_t ca = static_cast<size_t>(j0 + jj) * n + i;
+        K = (static_cast<double>(e.a_hi[ca]) + static_cast<double>(e.a_lo[ca])) - K;
+      }
+      const double G = e.v_in[r0 + jj] + e.dt * K;
+      double V = G;
+      if (e.euler_last) {
+        e.g_out[r0 + jj] = G;
+        if (e.d_in) V = G + e.d_in[r0 + jj];
+        if (e.u_old) {
+          const double dl = V - e.u_old[r0 + jj];
+          s0 += dl * dl;
+          s1 += V * V;
+        }
+      }
+      e.v_out[r0 + jj] = V;
+      Vn[jj] = V;
+    }
+  }
+  if (!e.terms_r && !e.terms_l) return;
+#pragma unroll
+  for (int h8 = 0; h8 < 4; ++h8) {
+    Terms3 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = split3_f64(Vn[8 * h8 + u]);
+    if (e.terms_r) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (8 * h8 + u < cnt) put_r(e, 0, i, j0 + 8 * h8 + u, t[u]);
+    }
+    if (e.terms_l) {
+      const size_t off = static_cast<size_t>(i) * e.ldp + j0 + 8 * h8;
+      if (8 * h8 + 8 <= cnt) {
+        put_l8(e, off, t);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (8 * h8 + u < cnt) put_l1(e, off + u, t[u]);
+      }
+    }
   }
 }
 
-// One forward-Euler substep G = V + dt Fl(V) (single slice, row-major float64); on the
-// last substep also G_n out, the correction V_{n+1} = G_n + D_n and the norm terms.
-__device__ __forceinline__ void euler_elem(const EpiParams &e, int i, int j, float v, double &s0,
-                                           double &s1) {
-  const int n = e.n;
-  const size_t r = static_cast<size_t>(i) * n + j;
-  double K = static_cast<double>(v);
-  if (e.flow == FA_FLOW_SQRT) {
-    const size_t c = static_cast<size_t>(j) * n + i;
-    K = (static_cast<double>(e.a_hi[c]) + static_cast<double>(e.a_lo[c])) - K;
-  }
-  const double G = e.v_in[r] + e.dt * K;
-  double Vn = G;
-  if (e.euler_last) {
-    e.g_out[r] = G;
-    if (e.d_in) Vn = G + e.d_in[r];
-    if (e.u_old) {
-      const double dl = Vn - e.u_old[r];
-      s0 += dl * dl;
-      s1 += Vn * Vn;
-    }
-  }
-  e.v_out[r] = Vn;
-  const int nt = e.terms_l > e.terms_r ? e.terms_l : e.terms_r;
-  if (nt) {
-    __nv_bfloat16 t[3];
-    split_f64(Vn, nt, t);
-    if (e.terms_r) put_r(e, 0, i, j, t);
-    if (e.terms_l) put_l(e, 0, i, j, t);
-  }
+// Bounded wait that, when `prof` is set, adds the cycles spent waiting to prof[slot].
+__device__ __forceinline__ bool pwait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                      unsigned long long *prof, int slot, unsigned sleep_ns = 0) {
+  if (!prof) return ptx::mbar_wait(bar, parity, abort_flag, sleep_ns);
+  const long long t0 = clock64();
+  const bool ok = ptx::mbar_wait(bar, parity, abort_flag, sleep_ns);
+  atomicAdd(prof + slot, static_cast<unsigned long long>(clock64() - t0));
+  return ok;
 }
 
 __device__ __forceinline__ void fail(volatile int *abort_flag, int *err) {
@@ -258,6 +311,7 @@ __device__ __forceinline__ void fail(volatile int *abort_flag, int *err) {
   if (err) atomicCAS(err, 0, static_cast<int>(FA_ERR_TIMEOUT));
 }
 
+// 10 warps: at most three per SM sub-partition, so up to 168 registers per thread.
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmL,
                    const __grid_constant__ CUtensorMap tmR,
@@ -265,16 +319,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  float *Ks = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + KS_BYTES);
-  uint64_t *empty = full + STAGES;
-  uint64_t *mbfull = empty + STAGES;
-  uint64_t *mbempty = mbfull + 2;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * TILE_BYTES);
+  uint64_t *kbempty = full + NSLOT;    // [NKB]: k-block consumed, its slots may be refilled
+  uint64_t *mbfull = kbempty + NKB;    // [2]
+  uint64_t *mbempty = mbfull + 2;      // [2]
   uint64_t *cbfull = mbempty + 2;
-  uint64_t *cbempty = cbfull + 2;
-  uint64_t *kfull = cbempty + 2;
-  uint64_t *kempty = kfull + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(kempty + 1);
+  uint64_t *cbempty = cbfull + 1;
+  uint64_t *finfull = cbempty + 1;
+  uint64_t *finempty = finfull + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(finempty + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   double *red = reinterpret_cast<double *>(tmem_slot + 2);
 
@@ -282,18 +335,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      ptx::mbar_init(full + s, 1);
-      ptx::mbar_init(empty + s, 1);
-    }
+    for (int s = 0; s < NSLOT; ++s) ptx::mbar_init(full + s, 1);
+    for (int s = 0; s < NKB; ++s) ptx::mbar_init(kbempty + s, 1);
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(mbfull + a, 1);
       ptx::mbar_init(mbempty + a, 128);
-      ptx::mbar_init(cbfull + a, 1);
-      ptx::mbar_init(cbempty + a, 128);
     }
-    ptx::mbar_init(kfull, 128);
-    ptx::mbar_init(kempty, 128);
+    ptx::mbar_init(cbfull, 1);
+    ptx::mbar_init(cbempty, 128);
+    ptx::mbar_init(finfull, 128);
+    ptx::mbar_init(finempty, STORE_WARPS * 32);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
@@ -310,13 +361,16 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int tiles_per_slice = p.mt * p.nt;
+  const long long t_kernel0 = clock64();
   const EpiParams &e = p.epi;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer: each k-block's term tiles, once ----------------
+    // Tile number g of the launch goes to ring slot g % NSLOT.  Before refilling a slot
+    // the producer waits until the k-block that last used it, (g - NSLOT) / ntl, has
+    // been consumed (barrier kbempty[k % NKB], phase k / NKB).
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      uint32_t g = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
         const int mt = tile % p.mt;
@@ -326,21 +380,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int lb = p.l_batched ? gb : 0;
         const int rb = p.r_batched ? gb : 0;
         for (int kb = 0; ok && kb < p.kblocks; ++kb) {
-          for (int q = 0; q < p.npairs; ++q) {
-            if (!ptx::mbar_wait(empty + stage, phase ^ 1u, abort_flag)) {
-              fail(abort_flag, e.err);
-              ok = false;
-              break;
+          for (int ti = 0; ti < p.ntl; ++ti, ++g) {
+            if (g >= static_cast<uint32_t>(NSLOT)) {
+              const uint32_t k = (g - NSLOT) / p.ntl;
+              if (!pwait(kbempty + k % NKB, (k / NKB) & 1u, abort_flag, p.prof, 0)) {
+                fail(abort_flag, e.err);
+                ok = false;
+                break;
+              }
             }
-            uint8_t *sl = smem + stage * STAGE_BYTES;
-            ptx::mbar_arrive_expect_tx(full + stage, STAGE_BYTES);
-            ptx::tma_load_4d(sl, &tmL, full + stage, kb * BK, mt * BM, lb, p.pair_a[q]);
-            ptx::tma_load_4d(sl + L_BYTES, &tmR, full + stage, kb * BK, ntile * BN, rb,
-                             p.pair_b[q]);
-            if (++stage == STAGES) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            const int slot = g % NSLOT;
+            ptx::mbar_arrive_expect_tx(full + slot, TILE_BYTES);
+            if (p.tl_side[ti] == 0)
+              ptx::tma_load_4d(smem + slot * TILE_BYTES, &tmL, full + slot, kb * BK, mt * BM, lb,
+                               p.tl_term[ti]);
+            else
+              ptx::tma_load_4d(smem + slot * TILE_BYTES, &tmR, full + slot, kb * BK, ntile * BN,
+                               rb, p.tl_term[ti]);
           }
         }
       }
@@ -348,76 +404,97 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      int stage = 0, mb = 0, ci = 0;
-      uint32_t phase = 0, mph = 0, cph = 0;
+    // The whole warp runs the loop (so its values stay warp-uniform); one elected lane
+    // issues the tcgen05 instructions.  Tile number g of the launch sits in ring slot
+    // g % NSLOT with phase (g / NSLOT) & 1; its descriptor is the ring's base descriptor
+    // plus slot * TILE_BYTES / 16.
+    {
+      const uint64_t desc0 = ptx::sdesc_sw128(ptx::smem_u32(smem));
+      uint32_t g = 0, kbi = 0;
+      int mb = 0;
+      uint32_t mph = 0, cph = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-        if (!ptx::mbar_wait(cbempty + ci, cph ^ 1u, abort_flag)) {
+        if (!pwait(cbempty, cph ^ 1u, abort_flag, lane == 0 ? p.prof : nullptr, 3)) {
           fail(abort_flag, e.err);
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t c_tmem = tmem_base + CB_COL0 + static_cast<uint32_t>(ci * BN);
         for (int kb = 0; ok && kb < p.kblocks; ++kb) {
-          if (!ptx::mbar_wait(mbempty + mb, mph ^ 1u, abort_flag)) {
-            fail(abort_flag, e.err);
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t m_tmem = tmem_base + MB_COL0 + static_cast<uint32_t>(mb * BN);
+          int waited = 0;
           for (int q = 0; q < p.npairs; ++q) {
-            if (!ptx::mbar_wait(full + stage, phase, abort_flag)) {
-              fail(abort_flag, e.err);
-              ok = false;
-              break;
+            const int need = p.pair_at[q];
+            for (; waited <= need; ++waited) {
+              const uint32_t gt = g + waited;
+              if (!pwait(full + gt % NSLOT, (gt / NSLOT) & 1u, abort_flag,
+                         lane == 0 ? p.prof : nullptr, 1)) {
+                fail(abort_flag, e.err);
+                ok = false;
+                break;
+              }
+            }
+            if (!ok) break;
+            uint32_t d;
+            if (q == 0) {
+              if (!pwait(mbempty + mb, mph ^ 1u, abort_flag, lane == 0 ? p.prof : nullptr, 2)) {
+                fail(abort_flag, e.err);
+                ok = false;
+                break;
+              }
+              d = tmem_base + MB_COL0 + static_cast<uint32_t>(mb * BN);
+            } else {
+              d = tmem_base + CB_COL;
             }
             ptx::tc_fence_after();
-            const uint32_t sl = ptx::smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t sr = sl + L_BYTES;
+            const uint64_t da =
+                desc0 + static_cast<uint64_t>(((g + p.pair_tl[q]) % NSLOT) * (TILE_BYTES >> 4));
+            const uint64_t db =
+                desc0 + static_cast<uint64_t>(((g + p.pair_tr[q]) % NSLOT) * (TILE_BYTES >> 4));
+            if (ptx::elect_one()) {
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint32_t acc = (q == 0) ? (k > 0) : (kb > 0 || q > 1 || k > 0);
-              ptx::tc_mma_bf16(q == 0 ? m_tmem : c_tmem, ptx::sdesc_sw128(sl + k * 32),
-                               ptx::sdesc_sw128(sr + k * 32), p.idesc, acc);
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                // K-step kk starts 32 bytes further into the 128-byte swizzled rows.
+                const uint32_t acc = (q == 0) ? (kk > 0) : (kb > 0 || q > 1 || kk > 0);
+                ptx::tc_mma_bf16(d, da + 2u * kk, db + 2u * kk, p.idesc, acc);
+              }
+              if (q == 0) ptx::tc_commit(mbfull + mb);
             }
-            ptx::tc_commit(empty + stage);
-            if (q == 0) ptx::tc_commit(mbfull + mb);
-            if (++stage == STAGES) {
-              stage = 0;
-              phase ^= 1u;
-            }
+            __syncwarp();
           }
+          if (!ok) break;
+          if (ptx::elect_one()) ptx::tc_commit(kbempty + kbi % NKB);
+          __syncwarp();
+          ++kbi;
+          g += p.ntl;
           mb ^= 1;
           if (mb == 0) mph ^= 1u;
         }
         if (!ok) break;
-        ptx::tc_commit(cbfull + ci);
-        ci ^= 1;
-        if (ci == 0) cph ^= 1u;
+        if (ptx::elect_one()) ptx::tc_commit(cbfull);
+        __syncwarp();
+        cph ^= 1u;
       }
     }
-    __syncwarp();
   } else if (warp < 6) {
-    // ---------------- drain: TMEM -> float32 registers -> shared hand-off tile ----------------
+    // ---------------- drain: main chunks -> float32 registers; + corrections -> finished tile ----
     const int q = warp & 3;              // TMEM lanes [32q, 32q + 32) are reachable from this warp
-    const int row = q * 32 + lane;
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
-    int mb = 0, ci = 0;
-    uint32_t mph = 0, cph = 0, kph = 0;
+    unsigned long long *prof = (warp == 2 && lane == 0) ? p.prof : nullptr;
+    int mb = 0;
+    uint32_t mph = 0, cph = 0, fph = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
       for (int kb = 0; kb < p.kblocks; ++kb) {
-        if (!ptx::mbar_wait(mbfull + mb, mph, abort_flag)) {
+        if (!pwait(mbfull + mb, mph, abort_flag, prof, 4, 20)) {
           fail(abort_flag, e.err);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
+        const long long td = clock64();
 #pragma unroll
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
@@ -425,13 +502,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int u = 0; u < 32; ++u) acc[c * 32 + u] += v[u];
         }
+        if (prof) atomicAdd(prof + 9, static_cast<unsigned long long>(clock64() - td));
         ptx::tc_fence_before();
         ptx::mbar_arrive(mbempty + mb);
         mb ^= 1;
         if (mb == 0) mph ^= 1u;
       }
       if (!ok) break;
-      if (!ptx::mbar_wait(cbfull + ci, cph, abort_flag)) {
+      if (!pwait(cbfull, cph, abort_flag, prof, 5, 20)) {
         fail(abort_flag, e.err);
         break;
       }
@@ -440,135 +518,100 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
-          ptx::tmem_ld_32x32b_x32(lane_base + CB_COL0 + static_cast<uint32_t>(ci * BN + c * 32), v);
+          ptx::tmem_ld_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
 #pragma unroll
           for (int u = 0; u < 32; ++u) acc[c * 32 + u] += v[u];
         }
       }
       ptx::tc_fence_before();
-      ptx::mbar_arrive(cbempty + ci);
-      ci ^= 1;
-      if (ci == 0) cph ^= 1u;
-      if (!ptx::mbar_wait(kempty, kph ^ 1u, abort_flag)) {
+      ptx::mbar_arrive(cbempty);
+      cph ^= 1u;
+      if (!pwait(finempty, fph ^ 1u, abort_flag, prof, 6, 100)) {
         fail(abort_flag, e.err);
         break;
       }
+      ptx::tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < BN; ++c) Ks[c * KS_LD + row] = acc[c];
-      ptx::mbar_arrive(kfull);
-      kph ^= 1u;
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) v[u] = acc[c * 32 + u];
+        ptx::tmem_st_32x32b_x32(lane_base + FIN_COL + static_cast<uint32_t>(c * 32), v);
+      }
+      ptx::tmem_wait_st();
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(finfull);
+      fph ^= 1u;
     }
   } else {
-    // ---------------- store: epilogue from the shared tile to global memory ----------------
-    const int t = threadIdx.x - 192;     // 0..127
-    const int sw = t >> 5;
-    uint32_t kph = 0;
+    // ---------------- store: finished tile (TMEM, one row per thread) -> global memory ----------
+    const int q = warp & 3;
+    const int sw = warp - 6;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
     const int n = e.n;
-    const bool pass1 = (e.mode == EPI_STAGE || e.mode == EPI_PROD);
-    const bool pass2 = (e.mode == EPI_STAGE && e.terms_l && !e.last) || e.mode == EPI_EULER ||
-                       e.mode == EPI_STORE;
     const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
+    unsigned long long *prof = (warp == 6 && lane == 0) ? p.prof : nullptr;
+    uint32_t fph = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
       const int mt = tile % p.mt;
       const int rest = tile / p.mt;
       const int ntile = rest % p.nt;
       const int lb = rest / p.nt;
       const int gb = e.b0 + lb;
-      const int m0 = mt * BM, n0 = ntile * BN;
-      if (!ptx::mbar_wait(kfull, kph, abort_flag)) {
+      const int i = mt * BM + row;
+      if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
         fail(abort_flag, e.err);
         break;
       }
+      ptx::tc_fence_after();
+      const long long ts = clock64();
       double s0 = 0.0, s1 = 0.0;
-      if (pass1) {
-        // Four rows per thread (16-byte column-major accesses), columns c = sw + 4k,
-        // processed UNR at a time with their global loads issued together.
-        const int sub = t & 31;
-        const int r0 = 4 * sub;
-        const int i0 = m0 + r0;
-        const bool vec = ((n & 3) == 0) && (i0 + 3 < n);
-        const int nt = e.terms_l > e.terms_r ? e.terms_l : e.terms_r;
-        constexpr int UNR = 4;
-        if (vec) {
-          const size_t nn = static_cast<size_t>(n) * n;
-          for (int k0 = 0; k0 < BN / 4; k0 += UNR) {
-            Quad qd[UNR];
-            size_t cc[UNR];
-            bool act[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-              const int c = sw + 4 * (k0 + u);
-              const int j = n0 + c;
-              act[u] = j < n;
-              cc[u] = gb * nn + static_cast<size_t>(j) * n + i0;
-              if (act[u] && e.mode == EPI_STAGE) stage_quad_load(e, cc[u], qd[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-              if (!act[u]) continue;
-              const int c = sw + 4 * (k0 + u);
-              const int j = n0 + c;
-              float v[4], y[4];
-#pragma unroll
-              for (int w = 0; w < 4; ++w) v[w] = Ks[c * KS_LD + r0 + w];
-              if (e.mode == EPI_STAGE) {
-                stage_quad_finish(e, gb, i0, j, cc[u], v, qd[u], y);
-                if (!e.last) {
-                  if (e.terms_r) put_r_quad(e, gb, i0, j, y, nt);
-#pragma unroll
-                  for (int w = 0; w < 4; ++w) Ks[c * KS_LD + r0 + w] = y[w];
-                }
+      for (int c = 0; c < BN / 32; ++c) {
+        const int j0 = ntile * BN + c * 32;
+        float v[32];
+        ptx::tmem_ld_32x32b_x32(lane_base + FIN_COL + static_cast<uint32_t>(c * 32), v);
+        if (j0 >= n || i >= n) continue;
+        const int cnt = (n - j0) < 32 ? (n - j0) : 32;
+        if (e.mode == EPI_STAGE) {
+          const bool sq = e.flow == FA_FLOW_SQRT;
+          switch (e.stage) {
+            case 1: sq ? stage_chunk<1, true, false>(e, gb, i, j0, cnt, v)
+                       : stage_chunk<1, false, false>(e, gb, i, j0, cnt, v); break;
+            case 2: sq ? stage_chunk<2, true, false>(e, gb, i, j0, cnt, v)
+                       : stage_chunk<2, false, false>(e, gb, i, j0, cnt, v); break;
+            case 3: sq ? stage_chunk<3, true, false>(e, gb, i, j0, cnt, v)
+                       : stage_chunk<3, false, false>(e, gb, i, j0, cnt, v); break;
+            default:
+              if (e.last) {
+                sq ? stage_chunk<4, true, true>(e, gb, i, j0, cnt, v)
+                   : stage_chunk<4, false, true>(e, gb, i, j0, cnt, v);
               } else {
-                put_r_quad(e, gb, i0, j, v, e.terms_r);
+                sq ? stage_chunk<4, true, false>(e, gb, i, j0, cnt, v)
+                   : stage_chunk<4, false, false>(e, gb, i, j0, cnt, v);
               }
-            }
           }
+        } else if (e.mode == EPI_PROD) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            if (jj < cnt) put_r(e, gb, i, j0 + jj, split3_f32(v[jj]));
+        } else if (e.mode == EPI_EULER) {
+          euler_chunk(e, i, j0, cnt, v, s0, s1);
         } else {
-          for (int k = 0; k < BN / 4; ++k) {
-            const int c = sw + 4 * k;
-            const int j = n0 + c;
-            if (j >= n) break;
-            for (int w = 0; w < 4; ++w) {
-              const int i = i0 + w;
-              if (i >= n) break;
-              const float v = Ks[c * KS_LD + r0 + w];
-              if (e.mode == EPI_STAGE) {
-                Ks[c * KS_LD + r0 + w] = stage_elem(e, gb, i, j, v);
-              } else {
-                __nv_bfloat16 tt[3];
-                split_f32(v, e.terms_r, tt);
-                put_r(e, gb, i, j, tt);
-              }
-            }
-          }
+          const size_t r0 = gb * static_cast<size_t>(n) * n + static_cast<size_t>(i) * n + j0;
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            if (jj < cnt)
+              e.store_out[r0 + jj] =
+                  e.alpha * static_cast<double>(v[jj]) + (i == j0 + jj ? e.beta : 0.0);
         }
       }
-      if (pass2) {
-        ptx::named_bar_sync(2, 128);
-        // warp = 32 rows, lanes across columns: row-major outputs are coalesced
-        for (int rr = 0; rr < 32; ++rr) {
-          const int r = sw * 32 + rr;
-          const int i = m0 + r;
-          if (i >= n) break;
-#pragma unroll
-          for (int qq = 0; qq < BN / 32; ++qq) {
-            const int c = lane + 32 * qq;
-            const int j = n0 + c;
-            if (j < n) {
-              const float v = Ks[c * KS_LD + r];
-              if (e.mode == EPI_STAGE) {
-                __nv_bfloat16 tt[3];
-                split_f32(v, e.terms_l > e.terms_r ? e.terms_l : e.terms_r, tt);
-                put_l(e, gb, i, j, tt);
-              } else if (e.mode == EPI_EULER) {
-                euler_elem(e, i, j, v, s0, s1);
-              } else {
-                e.store_out[gb * static_cast<size_t>(n) * n + static_cast<size_t>(i) * n + j] =
-                    e.alpha * static_cast<double>(v) + (i == j ? e.beta : 0.0);
-              }
-            }
-          }
-        }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(finempty);
+      fph ^= 1u;
+      if (prof) {
+        atomicAdd(prof + 8, static_cast<unsigned long long>(clock64() - ts));
+        atomicAdd(prof + 11, 1ull);
       }
       if (norms) {
 #pragma unroll
@@ -580,17 +623,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           red[2 * sw] = s0;
           red[2 * sw + 1] = s1;
         }
-        ptx::named_bar_sync(2, 128);
-        if (t == 0) {
-          const double t0 = ((red[0] + red[2]) + red[4]) + red[6];
-          const double t1 = ((red[1] + red[3]) + red[5]) + red[7];
-          const size_t slot = static_cast<size_t>(lb) * tiles_per_slice + (tile % tiles_per_slice);
-          e.norm_part[2 * slot] = t0;
-          e.norm_part[2 * slot + 1] = t1;
+        ptx::named_bar_sync(2, STORE_WARPS * 32);
+        if (sw == 0 && lane == 0) {
+          double t0 = 0.0, t1 = 0.0;
+          for (int w = 0; w < STORE_WARPS; ++w) {
+            t0 += red[2 * w];
+            t1 += red[2 * w + 1];
+          }
+          const size_t slotn = static_cast<size_t>(lb) * tiles_per_slice + (tile % tiles_per_slice);
+          e.norm_part[2 * slotn] = t0;
+          e.norm_part[2 * slotn + 1] = t1;
         }
+        ptx::named_bar_sync(2, STORE_WARPS * 32);
       }
-      ptx::mbar_arrive(kempty);
-      kph ^= 1u;
     }
   }
 
@@ -602,6 +647,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   ptx::tc_fence_before();
   __syncthreads();
+  if (p.prof && threadIdx.x == 0)
+    atomicAdd(p.prof + 10, static_cast<unsigned long long>(clock64() - t_kernel0));
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem_base, TMEM_COLS);
@@ -693,6 +740,47 @@ __global__ void load_state_kernel(const double *__restrict__ U, int n, int ldp, 
 }
 
 }  // namespace
+
+void tc_schedule(const PairSet &ps, TcGemmParams &g) {
+  // Tile load order: L0, R0, then whatever the next pair in order needs.
+  int pos[2][3];
+  for (int s = 0; s < 2; ++s)
+    for (int t = 0; t < 3; ++t) pos[s][t] = -1;
+  g.ntl = 0;
+  auto need = [&](int side, int term) {
+    if (pos[side][term] < 0) {
+      pos[side][term] = g.ntl;
+      g.tl_side[g.ntl] = side;
+      g.tl_term[g.ntl] = term;
+      ++g.ntl;
+    }
+  };
+  for (int k = 0; k < ps.npairs; ++k) {
+    need(0, ps.a[k]);
+    need(1, ps.b[k]);
+  }
+  // Pairs in issue order: by the position of the later of their two tiles (the main
+  // product, pair 0, stays first).
+  g.npairs = ps.npairs;
+  int order[kMaxPairs];
+  for (int k = 0; k < ps.npairs; ++k) order[k] = k;
+  for (int x = 1; x < ps.npairs; ++x)
+    for (int y = x; y > 1; --y) {
+      const int ka = order[y - 1], kb = order[y];
+      const int pa = pos[0][ps.a[ka]] > pos[1][ps.b[ka]] ? pos[0][ps.a[ka]] : pos[1][ps.b[ka]];
+      const int pb = pos[0][ps.a[kb]] > pos[1][ps.b[kb]] ? pos[0][ps.a[kb]] : pos[1][ps.b[kb]];
+      if (pb < pa) {
+        order[y - 1] = kb;
+        order[y] = ka;
+      }
+    }
+  for (int k = 0; k < ps.npairs; ++k) {
+    const int o = order[k];
+    g.pair_tl[k] = pos[0][ps.a[o]];
+    g.pair_tr[k] = pos[1][ps.b[o]];
+    g.pair_at[k] = g.pair_tl[k] > g.pair_tr[k] ? g.pair_tl[k] : g.pair_tr[k];
+  }
+}
 
 PairSet pair_set(int dtype) {
   PairSet s{};
