@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * TILE_BYTES);
-  uint64_t *kbempty = full + NSLOT;    // [NKB]: k-block consumed, its slots may be refilled
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * TILE_BYTES);   // [NKB]
+  uint64_t *kbempty = full + NKB;      // [NKB]: k-block consumed, its slots may be refilled
   uint64_t *mbfull = kbempty + NKB;    // [2]
   uint64_t *mbempty = mbfull + 2;      // [2]
   uint64_t *cbfull = mbempty + 2;
@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSLOT; ++s) ptx::mbar_init(full + s, 1);
-    for (int s = 0; s < NKB; ++s) ptx::mbar_init(kbempty + s, 1);
+    for (int s = 0; s < NKB; ++s) {
+      ptx::mbar_init(full + s, 1);
+      ptx::mbar_init(kbempty + s, 1);
+    }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(mbfull + a, 1);
       ptx::mbar_init(mbempty + a, 128);
@@ -366,11 +368,19 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer: each k-block's term tiles, once ----------------
-    // Tile number g of the launch goes to ring slot g % NSLOT.  Before refilling a slot
-    // the producer waits until the k-block that last used it, (g - NSLOT) / ntl, has
-    // been consumed (barrier kbempty[k % NKB], phase k / NKB).
+    // Tile number g of the launch goes to ring slot g % NSLOT; k-block number k (counted
+    // over the launch) signals barrier full[k % NKB] (phase k / NKB) once all its tiles
+    // have landed.  Before refilling a slot the producer waits until the k-block that last
+    // used it, (g - NSLOT) / ntl, has been consumed (kbempty, same indexing).
     if (lane == 0) {
-      uint32_t g = 0;
+      int side[6], term[6];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        side[t] = p.tl_side[t];
+        term[t] = p.tl_term[t];
+      }
+      const int ntl = p.ntl;
+      uint32_t g = 0, k = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
         const int mt = tile % p.mt;
@@ -379,93 +389,90 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int gb = e.b0 + rest / p.nt;
         const int lb = p.l_batched ? gb : 0;
         const int rb = p.r_batched ? gb : 0;
-        for (int kb = 0; ok && kb < p.kblocks; ++kb) {
-          for (int ti = 0; ti < p.ntl; ++ti, ++g) {
-            if (g >= static_cast<uint32_t>(NSLOT)) {
-              const uint32_t k = (g - NSLOT) / p.ntl;
-              if (!pwait(kbempty + k % NKB, (k / NKB) & 1u, abort_flag, p.prof, 0)) {
+        for (int kb = 0; ok && kb < p.kblocks; ++kb, ++k) {
+          uint64_t *fb = full + k % NKB;
+#pragma unroll
+          for (int ti = 0; ti < 6; ++ti) {
+            if (ti >= ntl || !ok) continue;
+            const uint32_t gt = g + ti;
+            if (gt >= static_cast<uint32_t>(NSLOT)) {
+              const uint32_t kp = (gt - NSLOT) / ntl;
+              if (!pwait(kbempty + kp % NKB, (kp / NKB) & 1u, abort_flag, p.prof, 0)) {
                 fail(abort_flag, e.err);
                 ok = false;
-                break;
+                continue;
               }
             }
-            const int slot = g % NSLOT;
-            ptx::mbar_arrive_expect_tx(full + slot, TILE_BYTES);
-            if (p.tl_side[ti] == 0)
-              ptx::tma_load_4d(smem + slot * TILE_BYTES, &tmL, full + slot, kb * BK, mt * BM, lb,
-                               p.tl_term[ti]);
+            if (ti == 0) ptx::mbar_arrive_expect_tx(fb, ntl * TILE_BYTES);
+            uint8_t *dst = smem + (gt % NSLOT) * TILE_BYTES;
+            if (side[ti] == 0)
+              ptx::tma_load_4d(dst, &tmL, fb, kb * BK, mt * BM, lb, term[ti]);
             else
-              ptx::tma_load_4d(smem + slot * TILE_BYTES, &tmR, full + slot, kb * BK, ntile * BN,
-                               rb, p.tl_term[ti]);
+              ptx::tma_load_4d(dst, &tmR, fb, kb * BK, ntile * BN, rb, term[ti]);
           }
+          g += ntl;
         }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    // The whole warp runs the loop (so its values stay warp-uniform); one elected lane
-    // issues the tcgen05 instructions.  Tile number g of the launch sits in ring slot
-    // g % NSLOT with phase (g / NSLOT) & 1; its descriptor is the ring's base descriptor
-    // plus slot * TILE_BYTES / 16.
+    // The whole warp runs the loop (its values stay warp-uniform); per k-block it waits
+    // once for the k-block's tiles and once for a free main chunk, then one elected lane
+    // issues every term pair's MMAs and the two commits.  Tile number g of the launch sits
+    // in ring slot g % NSLOT; its descriptor is the ring's base descriptor plus
+    // slot * TILE_BYTES / 16.
     {
+      int ptl[kMaxPairs], ptr[kMaxPairs];
+#pragma unroll
+      for (int q = 0; q < kMaxPairs; ++q) {
+        ptl[q] = p.pair_tl[q];
+        ptr[q] = p.pair_tr[q];
+      }
+      const int npairs = p.npairs, ntl = p.ntl;
+      const uint32_t idesc = p.idesc;
       const uint64_t desc0 = ptx::sdesc_sw128(ptx::smem_u32(smem));
-      uint32_t g = 0, kbi = 0;
+      uint32_t g = 0, k = 0;
       int mb = 0;
       uint32_t mph = 0, cph = 0;
       bool ok = true;
+      unsigned long long *prof = lane == 0 ? p.prof : nullptr;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-        if (!pwait(cbempty, cph ^ 1u, abort_flag, lane == 0 ? p.prof : nullptr, 3)) {
+        if (!pwait(cbempty, cph ^ 1u, abort_flag, prof, 3)) {
           fail(abort_flag, e.err);
           break;
         }
-        ptx::tc_fence_after();
-        for (int kb = 0; ok && kb < p.kblocks; ++kb) {
-          int waited = 0;
-          for (int q = 0; q < p.npairs; ++q) {
-            const int need = p.pair_at[q];
-            for (; waited <= need; ++waited) {
-              const uint32_t gt = g + waited;
-              if (!pwait(full + gt % NSLOT, (gt / NSLOT) & 1u, abort_flag,
-                         lane == 0 ? p.prof : nullptr, 1)) {
-                fail(abort_flag, e.err);
-                ok = false;
-                break;
-              }
-            }
-            if (!ok) break;
-            uint32_t d;
-            if (q == 0) {
-              if (!pwait(mbempty + mb, mph ^ 1u, abort_flag, lane == 0 ? p.prof : nullptr, 2)) {
-                fail(abort_flag, e.err);
-                ok = false;
-                break;
-              }
-              d = tmem_base + MB_COL0 + static_cast<uint32_t>(mb * BN);
-            } else {
-              d = tmem_base + CB_COL;
-            }
-            ptx::tc_fence_after();
-            const uint64_t da =
-                desc0 + static_cast<uint64_t>(((g + p.pair_tl[q]) % NSLOT) * (TILE_BYTES >> 4));
-            const uint64_t db =
-                desc0 + static_cast<uint64_t>(((g + p.pair_tr[q]) % NSLOT) * (TILE_BYTES >> 4));
-            if (ptx::elect_one()) {
-#pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-                // K-step kk starts 32 bytes further into the 128-byte swizzled rows.
-                const uint32_t acc = (q == 0) ? (kk > 0) : (kb > 0 || q > 1 || kk > 0);
-                ptx::tc_mma_bf16(d, da + 2u * kk, db + 2u * kk, p.idesc, acc);
-              }
-              if (q == 0) ptx::tc_commit(mbfull + mb);
-            }
-            __syncwarp();
+        for (int kb = 0; kb < p.kblocks; ++kb, ++k) {
+          if (!pwait(full + k % NKB, (k / NKB) & 1u, abort_flag, prof, 1) ||
+              !pwait(mbempty + mb, mph ^ 1u, abort_flag, prof, 2)) {
+            fail(abort_flag, e.err);
+            ok = false;
+            break;
           }
-          if (!ok) break;
-          if (ptx::elect_one()) ptx::tc_commit(kbempty + kbi % NKB);
+          ptx::tc_fence_after();
+          if (ptx::elect_one()) {
+            const uint32_t dmain = tmem_base + MB_COL0 + static_cast<uint32_t>(mb * BN);
+            const uint32_t dcorr = tmem_base + CB_COL;
+#pragma unroll
+            for (int q = 0; q < kMaxPairs; ++q) {
+              if (q < npairs) {
+                const uint64_t da =
+                    desc0 + static_cast<uint64_t>(((g + ptl[q]) % NSLOT) * (TILE_BYTES >> 4));
+                const uint64_t db =
+                    desc0 + static_cast<uint64_t>(((g + ptr[q]) % NSLOT) * (TILE_BYTES >> 4));
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                  // K-step kk starts 32 bytes further into the 128-byte swizzled rows.
+                  const uint32_t acc = (q == 0) ? (kk > 0) : (kb > 0 || q > 1 || kk > 0);
+                  ptx::tc_mma_bf16(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
+                }
+                if (q == 0) ptx::tc_commit(mbfull + mb);
+              }
+            }
+            ptx::tc_commit(kbempty + k % NKB);
+          }
           __syncwarp();
-          ++kbi;
-          g += p.ntl;
+          g += ntl;
           mb ^= 1;
           if (mb == 0) mph ^= 1u;
         }
