@@ -101,13 +101,14 @@ class Workload:
     tol: float        # stop when max_n ||U^{k+1}_n - U^k_n||_F / ||U^{k+1}_n||_F < tol
     seed: int = 0
     dtype: str = "f64"  # arithmetic of the propagators' products (fa_dtype name)
+    mixed_tol: float = 0.0  # stopping tolerance used with BF16 products (0 = use tol)
 
 
 # The five workloads, named by what they are.
 INV_N64 = Workload("inverse flow, n=64, lam~U[0.5,2], N=8, J=16, fp64", FLOW_INV, 64, "inv",
                    1.0, 8, 1, 16, 8, 1e-10)
 EXP_N2048 = Workload("exp flow, n=2048, lam~U[-4,0], N=64, J=64", FLOW_EXP, 2048, "exp",
-                     1.0, 64, 1, 64, 64, 1e-10, dtype="bf16x4")
+                     1.0, 64, 1, 64, 64, 1e-10, dtype="bf16x6", mixed_tol=1e-8)
 SQRT_N4096 = Workload("sqrt steady state, n=4096, lam~logU[1e-3,1], T=20, N=128, J=32",
                       FLOW_SQRT, 4096, "sqrt", 20.0, 128, 1, 32, 128, 1e-10)
 INV_N1024_WIDE = Workload("inverse flow, n=1024, lam~logU[1e-2,1], N=64, J=64", FLOW_INV,
