@@ -172,6 +172,22 @@ fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX
  * buffer (FA_FLOW_INV or FA_FLOW_SQRT); FA_ERR_UNSUPPORTED otherwise. */
 fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, double *dC);
 
+/* Allocation-free product dC = dL * dR for callers that cannot allocate device memory
+ * (their device memory is budgeted before start-up, or they hold only their inputs and
+ * outputs and cannot own a workspace).  The paper has no counterpart; this is a convenience
+ * of the library.  dL, dR, dC: n x n row-major float64 device arrays, 1 <= n <= 1024;
+ * dtype one of FA_BF16* (the tensor-core term products of the planned path, float32
+ * accumulation with the main product drained per 64-wide k-block).  The BF16 operand terms
+ * live in a fixed array inside the library (about 12 MB per GPU that loads it, held until
+ * process exit); no cudaMalloc, cudaFree or allocating library call is made.  The first call
+ * on a device looks the array up (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race.  FA_ERR_ARG for n outside [1, 1024], a non-BF16
+ * dtype or null pointers; FA_ERR_UNSUPPORTED on a device other than sm_103.  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy default stream). */
+fa_status fa_product_noalloc(int n, int dtype, const double *dL, const double *dR, double *dC,
+                             void *stream);
+
 /* Diagnostic: when d_counters (device, >= 16 unsigned 64-bit words, zeroed by the
  * caller) is not NULL, later tensor-core launches add per-role cycle counts to it:
  * [0] producer waiting for free slots, [1] MMA waiting for operand tiles, [2] MMA

@@ -83,6 +83,7 @@ struct Carver {
 
 namespace fa {
 void count_launch() { ++g_launches; }
+fa_status record_error(fa_status s, const char *msg) { return set_err(s, "%s", msg); }
 }  // namespace fa
 
 struct fa_plan_s {
@@ -190,6 +191,37 @@ size_t carve(fa_plan_s *p, char *base) {
 }
 
 fa_status encode(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nterms,
+                 size_t term_stride, int box_rows);
+
+}  // namespace
+
+namespace fa {
+fa_status encode_terms_map(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nterms,
+                           size_t term_stride, int box_rows) {
+  return encode(m, base, n, ldp, nslices, nterms, term_stride, box_rows);
+}
+
+TcGemmParams tc_launch_params(int n, int nb, int l_batched, int r_batched, const PairSet &ps) {
+  TcGemmParams g;
+  memset(&g, 0, sizeof(g));
+  g.n = n;
+  g.nb = nb;
+  g.l_batched = l_batched;
+  g.r_batched = r_batched;
+  g.mt = (n + TC_BM - 1) / TC_BM;
+  g.nt = (n + TC_BN - 1) / TC_BN;
+  g.num_tiles = g.mt * g.nt * nb;
+  g.kblocks = (n + 63) / 64;
+  tc_schedule(ps, g);
+  g.prof = g_prof;
+  g.idesc = ptx::idesc_bf16_f32(TC_BM, TC_BN);
+  return g;
+}
+}  // namespace fa
+
+namespace {
+
+fa_status encode(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nterms,
                  size_t term_stride, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return set_err(FA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
@@ -240,19 +272,7 @@ EpiParams base_epi(const fa_plan_s *p) {
 
 TcGemmParams tc_params(const fa_plan_s *p, int nb, int l_batched, int r_batched,
                        const EpiParams &e) {
-  TcGemmParams g;
-  memset(&g, 0, sizeof(g));
-  g.n = p->d.n;
-  g.nb = nb;
-  g.l_batched = l_batched;
-  g.r_batched = r_batched;
-  g.mt = (p->d.n + TC_BM - 1) / TC_BM;
-  g.nt = (p->d.n + TC_BN - 1) / TC_BN;
-  g.num_tiles = g.mt * g.nt * nb;
-  g.kblocks = (p->d.n + 63) / 64;
-  fa::tc_schedule(p->ps, g);
-  g.prof = g_prof;
-  g.idesc = fa::ptx::idesc_bf16_f32(TC_BM, TC_BN);
+  TcGemmParams g = fa::tc_launch_params(p->d.n, nb, l_batched, r_batched, p->ps);
   g.epi = e;
   return g;
 }

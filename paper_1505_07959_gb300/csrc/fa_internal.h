@@ -157,4 +157,12 @@ cudaError_t launch_identity(double *X, int n, cudaStream_t s);
 // Per-thread launch counter (incremented by every launcher).
 void count_launch();
 
+// Record a failure as the calling thread's last error; returns s.
+fa_status record_error(fa_status s, const char *msg);
+// 4-D tensor map over BF16 operand terms [nterms][nslices][n][ldp] with a 64 x box_rows box.
+fa_status encode_terms_map(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nterms,
+                           size_t term_stride, int box_rows);
+// Launch parameters of one tensor-core product over a pair set (no epilogue fields set).
+TcGemmParams tc_launch_params(int n, int nb, int l_batched, int r_batched, const PairSet &ps);
+
 }  // namespace fa

@@ -25,7 +25,7 @@ DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16
           "bf16x6": FA_BF16X6}
 SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_sweep",
            "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
-           "fa_debug_product", "fa_debug_set_profile", "fa_plan_destroy", "fa_status_string", "fa_last_error",
+           "fa_debug_product", "fa_debug_set_profile", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
            "fa_launch_count", "fa_launch_count_reset"]
 
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_parareal_solve_host": [vp, dp, dp, dp, ctypes.POINTER(fa_report)],
         "fa_debug_product": [vp, dp, dp, dp],
         "fa_debug_set_profile": [dp],
+        "fa_product_noalloc": [ctypes.c_int, ctypes.c_int, dp, dp, dp, vp],
         "fa_plan_destroy": [vp],
     }
     for name, args in sigs.items():
@@ -153,6 +154,12 @@ def fa_debug_product(h, dL, dR, dC):
 
 def fa_debug_set_profile(d_counters):
     _check(load_library().fa_debug_set_profile(_ptr(d_counters)))
+
+
+def fa_product_noalloc(n: int, dtype: int, dL, dR, dC, stream_handle: int):
+    """dC = dL @ dR through the library's fixed scratch array (no device allocation)."""
+    _check(load_library().fa_product_noalloc(n, dtype, _ptr(dL), _ptr(dR), _ptr(dC),
+                                             ctypes.c_void_p(stream_handle)))
 
 
 def fa_plan_destroy(h):
