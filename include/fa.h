@@ -198,6 +198,31 @@ fa_status fa_product_noalloc(int n, int dtype, const double *dL, const double *d
  * NULL switches it off. */
 fa_status fa_debug_set_profile(unsigned long long *d_counters);
 
+/* ---- Batches: many independent problems of mixed order and flow -------------------------
+ *
+ * Every RK4 stage and every coarse step of all problems runs as one persistent tensor-core
+ * launch over the union of their tiles (a ragged work list: each problem keeps its own order,
+ * operands and epilogue); from the second iteration on, one parareal iteration of the whole
+ * batch is replayed as a CUDA graph.  Problem i solves flow flows[i] on an ns[i] x ns[i]
+ * matrix to horizon Ts[i] with coarse_steps[i] Euler substeps per slice; all share N,
+ * fine_steps, max_iters, tol and the BF16 form `dtype`.  Convergence is per problem (its
+ * own max_n ||dU_n||_F / ||U_n||_F); the batch iterates until every problem converged or
+ * max_iters.  Same conventions as single plans: the caller binds one workspace. */
+typedef struct fa_batch_s *fa_batch_t;
+
+fa_status fa_batch_plan(fa_batch_t *out, int count, const int *ns, const int *flows,
+                        const double *Ts, const int *coarse_steps, int N, int fine_steps,
+                        int max_iters, double tol, int dtype, void *stream,
+                        size_t *workspace_bytes);
+fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_workspace, size_t bytes);
+/* dA[i] / dXout[i]: device pointers (host array of `count`), row-major float64 n_i x n_i.
+ * iters[i] (host, optional): iteration at which problem i met tol (or the count run);
+ * last_dx[i] (host, optional): its last convergence measure.  Returns FA_ERR_NOT_CONVERGED
+ * (outputs written) if some problem missed tol. */
+fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *dXout, int *iters,
+                         double *last_dx);
+fa_status fa_batch_destroy(fa_batch_t b);
+
 /* Release the plan (not the workspace, which the caller owns). */
 fa_status fa_plan_destroy(fa_plan_t p);
 

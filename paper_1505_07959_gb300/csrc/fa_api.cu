@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fa_internal.h"
 #include "fa_ptx.cuh"
@@ -495,6 +496,217 @@ fa_status refine(fa_plan_s *p, double *X) {
 
 }  // namespace
 
+
+// ---- batched solve: many problems of mixed order and flow --------------------------------------
+
+struct fa_batch_s {
+  struct Table {
+    size_t first = 0;   // index of the first segment in the device array
+    int nseg = 0;
+    int tiles = 0;
+  };
+  int count = 0, N = 0, J = 0, max_iters = 0, dtype = 0, max_m = 1;
+  double tol = 0.0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::vector<fa_plan_s *> plans;
+  std::vector<size_t> offs;
+  size_t ws_need = 0, seg_off = 0, norm_off = 0, dx_off = 0, err_off = 0, nseg_total = 0;
+  char *ws = nullptr;
+  fa::TcSegment *d_segs = nullptr;
+  fa::BatchNorm *d_norm = nullptr;
+  double *d_dx = nullptr;
+  int *d_err = nullptr;
+  Table fine[5][2];              // [stage 1..4, 4-last][phase: main, inverse second product]
+  std::vector<Table> coarse;     // [((mode * N + n) * max_m + sub) * 2 + phase]
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+  ~fa_batch_s() {
+    for (auto *p : plans) delete p;
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+  size_t coarse_index(int mode, int n, int sub, int phase) const {
+    return ((static_cast<size_t>(mode) * N + n) * max_m + sub) * 2 + phase;
+  }
+};
+
+namespace {
+
+void push_segment(std::vector<fa::TcSegment> &host, fa_batch_s::Table &t, const fa_plan_s *p,
+                  const CUtensorMap &L, const CUtensorMap &R, int nb, int lbat, int rbat,
+                  const EpiParams &e) {
+  fa::TcSegment sg;
+  memset(&sg, 0, sizeof(sg));
+  sg.tmL = L;
+  sg.tmR = R;
+  sg.epi = e;
+  sg.n = p->d.n;
+  sg.nb = nb;
+  sg.l_batched = lbat;
+  sg.r_batched = rbat;
+  sg.mt = (p->d.n + TC_BM - 1) / TC_BM;
+  sg.nt = (p->d.n + TC_BN - 1) / TC_BN;
+  sg.kblocks = (p->d.n + 63) / 64;
+  sg.tile_begin = t.tiles;
+  t.tiles += sg.mt * sg.nt * nb;
+  ++t.nseg;
+  host.push_back(sg);
+}
+
+// Segment tables of every launch of a batch iteration (fixed pointers: the coarse sweep
+// overwrites G in place, after the fine sweep has consumed it).
+void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
+  host.clear();
+  const int N = b->N, J = b->J;
+  // fine sweep: config c = stage 1..4 (c = 0..3), or stage 4 of the last step (c = 4)
+  for (int c = 0; c < 5; ++c) {
+    const int st = c < 4 ? c + 1 : 4;
+    const bool last = (c == 4);
+    const int cur = (st - 1) & 1;
+    for (int phase = 0; phase < 2; ++phase) {
+      fa_batch_s::Table &t = b->fine[c][phase];
+      t = fa_batch_s::Table();
+      t.first = host.size();
+      for (fa_plan_s *p : b->plans) {
+        const fa_problem_desc &d = p->d;
+        const double h = d.T / static_cast<double>(N) / static_cast<double>(J);
+        EpiParams e = base_epi(p);
+        e.mode = fa::EPI_STAGE;
+        e.stage = st;
+        e.last = last ? 1 : 0;
+        e.h = h;
+        e.ch = (st == 3) ? h : (st < 3 ? 0.5 * h : 0.0);
+        e.f_out = p->D;
+        e.g_old = p->Gold;
+        e.x_hi = p->x_hi;
+        e.x_lo = p->x_lo;
+        e.acc = p->acc;
+        e.a_hi = p->a_hi;
+        e.a_lo = p->a_lo;
+        e.out_r = p->Yr[cur ^ 1];
+        e.out_l = p->Yl[cur ^ 1];
+        e.terms_r = p->ps.terms_r;
+        e.terms_l = p->needs_l() ? p->ps.terms_l : 0;
+        e.term_stride_r = e.term_stride_l = p->strideY;
+        e.err = b->d_err;
+        if (phase == 0) {
+          if (d.flow == FA_FLOW_EXP) {
+            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e);
+          } else if (d.flow == FA_FLOW_SQRT) {
+            push_segment(host, t, p, p->tmYl[cur], p->tmYr[cur], N, 1, 1, e);
+          } else {
+            EpiParams e1 = base_epi(p);
+            e1.mode = fa::EPI_PROD;
+            e1.out_r = p->Pr;
+            e1.terms_r = p->ps.terms_r;
+            e1.term_stride_r = p->strideY;
+            e1.err = b->d_err;
+            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e1);
+          }
+        } else if (d.flow == FA_FLOW_INV) {
+          push_segment(host, t, p, p->tmYl[cur], p->tmPr, N, 1, 1, e);
+        }
+      }
+    }
+  }
+  // coarse sweep: mode 0 = Step 0, mode 1 = correction with norms
+  b->coarse.assign(static_cast<size_t>(2) * N * b->max_m * 2, fa_batch_s::Table());
+  for (int mode = 0; mode < 2; ++mode)
+    for (int n = 0; n < N; ++n)
+      for (int sub = 0; sub < b->max_m; ++sub)
+        for (int phase = 0; phase < 2; ++phase) {
+          fa_batch_s::Table &t = b->coarse[b->coarse_index(mode, n, sub, phase)];
+          t.first = host.size();
+          for (fa_plan_s *p : b->plans) {
+            const fa_problem_desc &d = p->d;
+            const int m = d.coarse_steps;
+            if (sub >= m) continue;
+            if (phase == 0 && d.flow != FA_FLOW_INV) continue;
+            const size_t nn = p->nn;
+            const int tglob = n * m + sub;
+            const int cur = tglob & 1;
+            const bool lastsub = (sub == m - 1);
+            if (phase == 0) {
+              EpiParams e1 = base_epi(p);
+              e1.mode = fa::EPI_PROD;
+              e1.out_r = p->Pcr;
+              e1.terms_r = p->ps.terms_r;
+              e1.term_stride_r = p->strideV;
+              e1.err = b->d_err;
+              push_segment(host, t, p, p->tmA, p->tmVr[cur], 1, 0, 0, e1);
+              continue;
+            }
+            EpiParams e = base_epi(p);
+            e.mode = fa::EPI_EULER;
+            e.dt = d.T / static_cast<double>(N) / static_cast<double>(m);
+            e.v_in = (sub == 0) ? p->U + static_cast<size_t>(n) * nn : p->Vtmp[(sub - 1) & 1];
+            e.v_out = lastsub ? p->U + static_cast<size_t>(n + 1) * nn : p->Vtmp[sub & 1];
+            e.euler_last = lastsub ? 1 : 0;
+            if (lastsub) {
+              e.g_out = p->Gold + static_cast<size_t>(n) * nn;
+              e.d_in = mode ? p->D + static_cast<size_t>(n) * nn : nullptr;
+              e.u_old = mode ? p->U + static_cast<size_t>(n + 1) * nn : nullptr;
+              e.norm_part = p->part + static_cast<size_t>(n) * p->part_tiles * 2;
+            }
+            e.a_hi = p->a_hi;
+            e.a_lo = p->a_lo;
+            e.out_r = p->Vr[cur ^ 1];
+            e.out_l = p->Vl[cur ^ 1];
+            e.terms_r = p->ps.terms_r;
+            e.terms_l = p->needs_l() ? p->ps.terms_l : 0;
+            e.term_stride_r = e.term_stride_l = p->strideV;
+            e.err = b->d_err;
+            if (d.flow == FA_FLOW_EXP)
+              push_segment(host, t, p, p->tmA, p->tmVr[cur], 1, 0, 0, e);
+            else if (d.flow == FA_FLOW_SQRT)
+              push_segment(host, t, p, p->tmVl[cur], p->tmVr[cur], 1, 0, 0, e);
+            else
+              push_segment(host, t, p, p->tmVl[cur], p->tmPcr, 1, 0, 0, e);
+          }
+        }
+}
+
+fa_status launch_table(fa_batch_s *b, const fa_batch_s::Table &t) {
+  if (t.nseg == 0) return FA_OK;
+  TcGemmParams g = fa::tc_launch_params(128, 1, 0, 0, b->plans[0]->ps);
+  g.epi.err = b->d_err;
+  FA_CUDA(fa::launch_tc_gemm_ragged(b->d_segs + t.first, t.nseg, t.tiles, g, b->num_sms,
+                                    b->stream));
+  return FA_OK;
+}
+
+fa_status batch_coarse(fa_batch_s *b, int mode) {
+  for (fa_plan_s *p : b->plans) {
+    FA_CUDA(fa::launch_split_terms(p->U, 1, p->d.n, p->ldp, p->Vl[0],
+                                   p->needs_l() ? p->ps.terms_l : 0, p->strideV, p->Vr[0],
+                                   p->ps.terms_r, p->strideV, 0, b->stream));
+  }
+  for (int n = 0; n < b->N; ++n)
+    for (int sub = 0; sub < b->max_m; ++sub)
+      for (int phase = 0; phase < 2; ++phase)
+        FA_TRY(launch_table(b, b->coarse[b->coarse_index(mode, n, sub, phase)]));
+  return FA_OK;
+}
+
+fa_status batch_iteration(fa_batch_s *b) {
+  for (fa_plan_s *p : b->plans) {
+    FA_CUDA(fa::launch_load_state(p->U, b->N, p->d.n, p->ldp, p->x_hi, p->x_lo, p->Yl[0],
+                                  p->needs_l() ? p->ps.terms_l : 0, p->strideY, p->Yr[0],
+                                  p->ps.terms_r, p->strideY, b->stream));
+  }
+  for (int j = 0; j < b->J; ++j)
+    for (int st = 1; st <= 4; ++st) {
+      const int c = (st == 4 && j == b->J - 1) ? 4 : st - 1;
+      FA_TRY(launch_table(b, b->fine[c][0]));
+      FA_TRY(launch_table(b, b->fine[c][1]));
+    }
+  FA_TRY(batch_coarse(b, 1));
+  FA_CUDA(fa::launch_batch_norms(b->d_norm, b->count, b->N, b->d_dx, b->d_err, b->stream));
+  return FA_OK;
+}
+
+}  // namespace
+
 // ---- C ABI -----------------------------------------------------------------------------------
 
 extern "C" {
@@ -735,6 +947,187 @@ fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, doub
 
 fa_status fa_debug_set_profile(unsigned long long *d_counters) {
   g_prof = d_counters;
+  return FA_OK;
+}
+
+
+fa_status fa_batch_plan(fa_batch_t *out, int count, const int *ns, const int *flows,
+                        const double *Ts, const int *coarse_steps, int N, int fine_steps,
+                        int max_iters, double tol, int dtype, void *stream,
+                        size_t *workspace_bytes) {
+  if (!out || !ns || !flows || !Ts || !coarse_steps || !workspace_bytes)
+    return set_err(FA_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (count < 1) return set_err(FA_ERR_ARG, "count must be >= 1");
+  if (dtype < FA_BF16 || dtype > FA_BF16X6)
+    return set_err(FA_ERR_ARG, "batched solves use a BF16 form (FA_BF16*)");
+  fa_batch_s *b = new (std::nothrow) fa_batch_s();
+  if (!b) return set_err(FA_ERR_ARG, "out of host memory");
+  b->count = count;
+  b->N = N;
+  b->J = fine_steps;
+  b->max_iters = max_iters;
+  b->tol = tol;
+  b->dtype = dtype;
+  b->stream = static_cast<cudaStream_t>(stream);
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    fa_problem_desc d{};
+    d.n = ns[i];
+    d.flow = flows[i];
+    d.T = Ts[i];
+    d.N = N;
+    d.coarse_steps = coarse_steps[i];
+    d.fine_steps = fine_steps;
+    d.max_iters = max_iters;
+    d.tol = tol;
+    d.fine_dtype = dtype;
+    d.coarse_dtype = dtype;
+    d.refine_steps = 0;
+    fa_plan_t p = nullptr;
+    size_t need = 0;
+    const fa_status st = fa_plan(&p, &d, stream, &need);
+    if (st != FA_OK) {
+      delete b;
+      return set_err(st, "problem %d: %s", i, fa_last_error());
+    }
+    b->plans.push_back(p);
+    b->offs.push_back(off);
+    off += (need + 255) & ~static_cast<size_t>(255);
+    if (d.coarse_steps > b->max_m) b->max_m = d.coarse_steps;
+    b->num_sms = p->num_sms;
+  }
+  // segment tables: fine 10 x count, coarse 2 x N x max_m x 2 x count (upper bound)
+  b->nseg_total = static_cast<size_t>(count) * (10 + 4 * static_cast<size_t>(N) * b->max_m);
+  b->seg_off = off;
+  off += b->nseg_total * sizeof(fa::TcSegment);
+  off = (off + 255) & ~static_cast<size_t>(255);
+  b->norm_off = off;
+  off += static_cast<size_t>(count) * sizeof(fa::BatchNorm);
+  off = (off + 255) & ~static_cast<size_t>(255);
+  b->dx_off = off;
+  off += static_cast<size_t>(count) * sizeof(double);
+  off = (off + 255) & ~static_cast<size_t>(255);
+  b->err_off = off;
+  off += 256;
+  b->ws_need = off;
+  *workspace_bytes = off;
+  *out = b;
+  return FA_OK;
+}
+
+fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_ws, size_t bytes) {
+  if (!b) return set_err(FA_ERR_ARG, "null batch");
+  if (!d_ws) return set_err(FA_ERR_WORKSPACE, "null workspace");
+  if (bytes < b->ws_need)
+    return set_err(FA_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", bytes, b->ws_need);
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255)
+    return set_err(FA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  b->ws = static_cast<char *>(d_ws);
+  b->d_segs = reinterpret_cast<fa::TcSegment *>(b->ws + b->seg_off);
+  b->d_norm = reinterpret_cast<fa::BatchNorm *>(b->ws + b->norm_off);
+  b->d_dx = reinterpret_cast<double *>(b->ws + b->dx_off);
+  b->d_err = reinterpret_cast<int *>(b->ws + b->err_off);
+  for (int i = 0; i < b->count; ++i) {
+    fa_plan_s *p = b->plans[i];
+    FA_TRY(fa_plan_bind_workspace(p, b->ws + b->offs[i], p->ws_need));
+  }
+  std::vector<fa::TcSegment> host;
+  host.reserve(b->nseg_total);
+  build_tables(b, host);
+  if (host.size() > b->nseg_total) return set_err(FA_ERR_WORKSPACE, "segment table overflow");
+  FA_CUDA(cudaMemcpyAsync(b->d_segs, host.data(), host.size() * sizeof(fa::TcSegment),
+                          cudaMemcpyHostToDevice, b->stream));
+  std::vector<fa::BatchNorm> norms(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    norms[i].part = b->plans[i]->part;
+    norms[i].tiles = b->plans[i]->part_tiles;
+  }
+  FA_CUDA(cudaMemcpyAsync(b->d_norm, norms.data(), norms.size() * sizeof(fa::BatchNorm),
+                          cudaMemcpyHostToDevice, b->stream));
+  FA_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->graph_tried = false;
+  return FA_OK;
+}
+
+fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *dXout, int *iters,
+                         double *last_dx) {
+  if (!b) return set_err(FA_ERR_ARG, "null batch");
+  if (!b->ws) return set_err(FA_ERR_WORKSPACE, "no workspace bound");
+  if (!dA || !dXout) return set_err(FA_ERR_ARG, "null pointer");
+  FA_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+  for (int i = 0; i < b->count; ++i) {
+    fa_plan_s *p = b->plans[i];
+    if (!dA[i] || !dXout[i]) return set_err(FA_ERR_ARG, "null pointer for problem %d", i);
+    p->err = b->d_err;
+    FA_TRY(fa_plan_set_matrix(p, dA[i]));
+    FA_CUDA(fa::launch_identity(p->U, p->d.n, b->stream));
+  }
+  FA_TRY(batch_coarse(b, 0));       // Step 0 (eq. eqStep0) for every problem
+  std::vector<double> dx(b->count, INFINITY);
+  std::vector<int> conv_at(b->count, 0);
+  int done = 0, k = 0;
+  for (; k < b->max_iters && done < b->count; ++k) {
+    if (b->graph) {
+      FA_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    } else if (!b->graph_tried && k > 0 && b->stream) {
+      // capture one iteration (every launch has fixed arguments) and replay it from now on
+      b->graph_tried = true;
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const fa_status st = batch_iteration(b);
+        const cudaError_t ce = cudaStreamEndCapture(b->stream, &gr);
+        if (st != FA_OK) return st;
+        if (ce == cudaSuccess && gr &&
+            cudaGraphInstantiate(&b->graph, gr, 0) == cudaSuccess) {
+          cudaGraphDestroy(gr);
+          FA_CUDA(cudaGraphLaunch(b->graph, b->stream));
+        } else {
+          if (gr) cudaGraphDestroy(gr);
+          b->graph = nullptr;
+          cudaGetLastError();
+          FA_TRY(batch_iteration(b));
+        }
+      } else {
+        cudaGetLastError();
+        FA_TRY(batch_iteration(b));
+      }
+    } else {
+      FA_TRY(batch_iteration(b));
+    }
+    FA_CUDA(cudaMemcpyAsync(dx.data(), b->d_dx, b->count * sizeof(double), cudaMemcpyDeviceToHost,
+                            b->stream));
+    FA_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->count; ++i) {
+      if (!conv_at[i] && dx[i] < b->tol) {
+        conv_at[i] = k + 1;
+        ++done;
+      }
+    }
+  }
+  for (int i = 0; i < b->count; ++i) {
+    fa_plan_s *p = b->plans[i];
+    FA_CUDA(cudaMemcpyAsync(dXout[i], p->U + static_cast<size_t>(b->N) * p->nn,
+                            p->nn * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    if (iters) iters[i] = conv_at[i] ? conv_at[i] : k;
+    if (last_dx) last_dx[i] = dx[i];
+  }
+  int h = 0;
+  FA_CUDA(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  FA_CUDA(cudaStreamSynchronize(b->stream));
+  if (h) return set_err(static_cast<fa_status>(h), "device error %d in the batch", h);
+  if (done < b->count && b->tol > 0.0)
+    return set_err(FA_ERR_NOT_CONVERGED, "%d of %d problems did not reach the tolerance",
+                   b->count - done, b->count);
+  return FA_OK;
+}
+
+fa_status fa_batch_destroy(fa_batch_t b) {
+  delete b;
   return FA_OK;
 }
 

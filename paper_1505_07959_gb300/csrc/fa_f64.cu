@@ -207,6 +207,33 @@ __global__ void max_ratio_kernel(const double *norms, int nslices, double *dx, i
   if (bad && err) atomicCAS(err, 0, static_cast<int>(FA_ERR_NONFINITE));
 }
 
+__global__ void batch_norms_kernel(const BatchNorm *bn, int count, int N, double *dx, int *err) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const double *part = bn[p].part;
+  const int tiles = bn[p].tiles;
+  double m = 0.0;
+  bool bad = false;
+  for (int b = threadIdx.x; b < N; b += blockDim.x) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int t = 0; t < tiles; ++t) {
+      t0 += part[2 * (static_cast<size_t>(b) * tiles + t)];
+      t1 += part[2 * (static_cast<size_t>(b) * tiles + t) + 1];
+    }
+    const double r = sqrt(t0) / sqrt(t1);
+    if (!isfinite(r)) bad = true;
+    if (r > m) m = r;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    bad = __any_sync(0xffffffffu, bad);
+  }
+  if (threadIdx.x == 0) {
+    dx[p] = bad ? CUDART_INF : m;
+    if (bad && err) atomicCAS(err, 0, static_cast<int>(FA_ERR_NONFINITE));
+  }
+}
+
 __global__ void i_minus_kernel(const double *A, int n, double *out) {
   const size_t nn = static_cast<size_t>(n) * n;
   for (size_t k = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; k < nn;
@@ -270,6 +297,14 @@ cudaError_t launch_reduce_norms(const double *part, int nslices, int tiles, doub
 cudaError_t launch_max_ratio(const double *norms, int nslices, double *dx, int *err,
                              cudaStream_t s) {
   max_ratio_kernel<<<1, 32, 0, s>>>(norms, nslices, dx, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_norms(const BatchNorm *bn, int count, int N, double *dx, int *err,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  batch_norms_kernel<<<count, 32, 0, s>>>(bn, count, N, dx, err);
   count_launch();
   return cudaGetLastError();
 }

@@ -78,6 +78,14 @@ struct EpiParams {
   int *err;                     // device error word
 };
 
+// One problem of a ragged (multi-problem) tensor-core launch: its tensor maps, epilogue
+// and shape, and the index of its first tile in the launch's tile sequence.
+struct alignas(64) TcSegment {
+  CUtensorMap tmL, tmR;
+  EpiParams epi;
+  int n, nb, l_batched, r_batched, mt, nt, kblocks, tile_begin;
+};
+
 // One tensor-core GEMM launch: for every slice b in [0, nb) and tile,
 // D = sum_p L_{a_p} R_{b_p}^T over the BF16 term pairs, then the epilogue.
 // Each 64-wide k-block loads its operand term tiles once (tl_side / tl_term,
@@ -98,6 +106,8 @@ struct TcGemmParams {
   int pair_tl[kMaxPairs], pair_tr[kMaxPairs], pair_at[kMaxPairs];
   uint32_t idesc;   // tcgen05 instruction descriptor
   unsigned long long *prof;   // optional per-role cycle counters (diagnostics), may be null
+  const TcSegment *segs;      // ragged launch: per-problem segments (device), else null
+  int nseg;
   EpiParams epi;
 };
 
@@ -124,6 +134,10 @@ void tc_schedule(const PairSet &ps, TcGemmParams &g);
 cudaError_t launch_tc_gemm(const CUtensorMap *tmL, const CUtensorMap *tmR,
                            const TcGemmParams &p, int num_sms, cudaStream_t s);
 cudaError_t launch_f64_gemm(const F64GemmParams &p, cudaStream_t s);
+// Ragged launch: `nseg` device segments holding `num_tiles` tiles in total (schedule fields of
+// `p` give the term tiles and pairs shared by all segments; p.epi.err the error word).
+cudaError_t launch_tc_gemm_ragged(const TcSegment *segs, int nseg, int num_tiles,
+                                  const TcGemmParams &p, int num_sms, cudaStream_t s);
 // Tile edge the float64 GEMM uses for (n, nb), and its tiles per slice.
 int f64_tile(int n, int nb);
 int f64_tiles_per_slice(int n, int nb);
@@ -145,6 +159,14 @@ cudaError_t launch_reduce_norms(const double *part, int nslices, int tiles_per_s
 // dx = max_b sqrt(norms[b][0] / norms[b][1]); flags non-finite values.
 cudaError_t launch_max_ratio(const double *norms, int nslices, double *dx, int *err,
                              cudaStream_t s);
+// Per-problem convergence measure of a batch: for problem p, dx[p] = max over its N slices of
+// sqrt(sum of d^2 partials / sum of v^2 partials), partials summed in a fixed order.
+struct BatchNorm {
+  const double *part;   // [N][tiles][2]
+  int tiles;
+};
+cudaError_t launch_batch_norms(const BatchNorm *bn, int count, int N, double *dx, int *err,
+                               cudaStream_t s);
 // I - A (row-major float64).
 cudaError_t launch_i_minus(const double *A, int n, double *out, cudaStream_t s);
 // Column-major float32 hi/lo copy of A (for K = A - X^2 in the mixed epilogue).

@@ -31,6 +31,8 @@
 //
 // TMEM columns: [0,128) and [128,256) main-product chunks (double-buffered),
 // [256,384) correction accumulator, [384,512) finished tile.
+#include <cstring>
+
 #include <cuda_bf16.h>
 
 #include "fa_internal.h"
@@ -296,6 +298,52 @@ __device__ __forceinline__ void euler_chunk(const EpiParams &e, int i, int j0, i
   }
 }
 
+// Where a tile of the launch lives: its problem's tensor maps and epilogue, and its position.
+struct TileInfo {
+  const CUtensorMap *tmL, *tmR;
+  const EpiParams *epi;
+  int mt, ntile, lslice, gb, lcoord, rcoord, kblocks, tiles_per_slice, tile_in_slice;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const TcGemmParams &p, const CUtensorMap *tmL,
+                                              const CUtensorMap *tmR, int tile) {
+  TileInfo t;
+  int local = tile, mtc = p.mt, ntc = p.nt, lbat = p.l_batched, rbat = p.r_batched;
+  if (p.segs) {
+    int lo = 0, hi = p.nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.segs[mid].tile_begin <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    const TcSegment *sg = p.segs + lo;
+    local = tile - sg->tile_begin;
+    mtc = sg->mt;
+    ntc = sg->nt;
+    lbat = sg->l_batched;
+    rbat = sg->r_batched;
+    t.tmL = &sg->tmL;
+    t.tmR = &sg->tmR;
+    t.epi = &sg->epi;
+    t.kblocks = sg->kblocks;
+  } else {
+    t.tmL = tmL;
+    t.tmR = tmR;
+    t.epi = &p.epi;
+    t.kblocks = p.kblocks;
+  }
+  t.tiles_per_slice = mtc * ntc;
+  t.tile_in_slice = local % t.tiles_per_slice;
+  t.mt = local % mtc;
+  const int rest = local / mtc;
+  t.ntile = rest % ntc;
+  t.lslice = rest / ntc;
+  t.gb = t.epi->b0 + t.lslice;
+  t.lcoord = lbat ? t.gb : 0;
+  t.rcoord = rbat ? t.gb : 0;
+  return t;
+}
+
 // Bounded wait that, when `prof` is set, adds the cycles spent waiting to prof[slot].
 __device__ __forceinline__ bool pwait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                       unsigned long long *prof, int slot, unsigned sleep_ns = 0) {
@@ -350,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && !p.segs) {
     ptx::prefetch_tmap(&tmL);
     ptx::prefetch_tmap(&tmR);
   }
@@ -362,9 +410,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int tiles_per_slice = p.mt * p.nt;
   const long long t_kernel0 = clock64();
-  const EpiParams &e = p.epi;
+  int *const err = p.epi.err;
 
   if (warp == 0) {
     // ---------------- TMA producer: each k-block's term tiles, once ----------------
@@ -383,13 +430,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t g = 0, k = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-        const int mt = tile % p.mt;
-        const int rest = tile / p.mt;
-        const int ntile = rest % p.nt;
-        const int gb = e.b0 + rest / p.nt;
-        const int lb = p.l_batched ? gb : 0;
-        const int rb = p.r_batched ? gb : 0;
-        for (int kb = 0; ok && kb < p.kblocks; ++kb, ++k) {
+        const TileInfo ti_ = tile_info(p, &tmL, &tmR, tile);
+        const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lcoord, rb = ti_.rcoord;
+        for (int kb = 0; ok && kb < ti_.kblocks; ++kb, ++k) {
           uint64_t *fb = full + k % NKB;
 #pragma unroll
           for (int ti = 0; ti < 6; ++ti) {
@@ -398,7 +441,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (gt >= static_cast<uint32_t>(NSLOT)) {
               const uint32_t kp = (gt - NSLOT) / ntl;
               if (!pwait(kbempty + kp % NKB, (kp / NKB) & 1u, abort_flag, p.prof, 0)) {
-                fail(abort_flag, e.err);
+                fail(abort_flag, err);
                 ok = false;
                 continue;
               }
@@ -406,9 +449,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (ti == 0) ptx::mbar_arrive_expect_tx(fb, ntl * TILE_BYTES);
             uint8_t *dst = smem + (gt % NSLOT) * TILE_BYTES;
             if (side[ti] == 0)
-              ptx::tma_load_4d(dst, &tmL, fb, kb * BK, mt * BM, lb, term[ti]);
+              ptx::tma_load_4d(dst, ti_.tmL, fb, kb * BK, mt * BM, lb, term[ti]);
             else
-              ptx::tma_load_4d(dst, &tmR, fb, kb * BK, ntile * BN, rb, term[ti]);
+              ptx::tma_load_4d(dst, ti_.tmR, fb, kb * BK, ntile * BN, rb, term[ti]);
           }
           g += ntl;
         }
@@ -438,14 +481,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       unsigned long long *prof = lane == 0 ? p.prof : nullptr;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+        const int kblocks = tile_info(p, &tmL, &tmR, tile).kblocks;
         if (!pwait(cbempty, cph ^ 1u, abort_flag, prof, 3)) {
-          fail(abort_flag, e.err);
+          fail(abort_flag, err);
           break;
         }
-        for (int kb = 0; kb < p.kblocks; ++kb, ++k) {
+        for (int kb = 0; kb < kblocks; ++kb, ++k) {
           if (!pwait(full + k % NKB, (k / NKB) & 1u, abort_flag, prof, 1) ||
               !pwait(mbempty + mb, mph ^ 1u, abort_flag, prof, 2)) {
-            fail(abort_flag, e.err);
+            fail(abort_flag, err);
             ok = false;
             break;
           }
@@ -491,12 +535,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t mph = 0, cph = 0, fph = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+      const int kblocks = tile_info(p, &tmL, &tmR, tile).kblocks;
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
-      for (int kb = 0; kb < p.kblocks; ++kb) {
+      for (int kb = 0; kb < kblocks; ++kb) {
         if (!pwait(mbfull + mb, mph, abort_flag, prof, 4, 20)) {
-          fail(abort_flag, e.err);
+          fail(abort_flag, err);
           ok = false;
           break;
         }
@@ -517,7 +562,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok) break;
       if (!pwait(cbfull, cph, abort_flag, prof, 5, 20)) {
-        fail(abort_flag, e.err);
+        fail(abort_flag, err);
         break;
       }
       ptx::tc_fence_after();
@@ -534,7 +579,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::mbar_arrive(cbempty);
       cph ^= 1u;
       if (!pwait(finempty, fph ^ 1u, abort_flag, prof, 6, 100)) {
-        fail(abort_flag, e.err);
+        fail(abort_flag, err);
         break;
       }
       ptx::tc_fence_after();
@@ -556,19 +601,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int sw = warp - 6;
     const int row = q * 32 + lane;
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
-    const int n = e.n;
-    const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
     unsigned long long *prof = (warp == 6 && lane == 0) ? p.prof : nullptr;
     uint32_t fph = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-      const int mt = tile % p.mt;
-      const int rest = tile / p.mt;
-      const int ntile = rest % p.nt;
-      const int lb = rest / p.nt;
-      const int gb = e.b0 + lb;
+      const TileInfo ti_ = tile_info(p, &tmL, &tmR, tile);
+      const EpiParams &e = *ti_.epi;
+      const int n = e.n;
+      const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
+      const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lslice, gb = ti_.gb;
       const int i = mt * BM + row;
       if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
-        fail(abort_flag, e.err);
+        fail(abort_flag, err);
         break;
       }
       ptx::tc_fence_after();
@@ -637,7 +680,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             t0 += red[2 * w];
             t1 += red[2 * w + 1];
           }
-          const size_t slotn = static_cast<size_t>(lb) * tiles_per_slice + (tile % tiles_per_slice);
+          const size_t slotn = static_cast<size_t>(lb) * ti_.tiles_per_slice + ti_.tile_in_slice;
           e.norm_part[2 * slotn] = t0;
           e.norm_part[2 * slotn + 1] = t1;
         }
@@ -826,6 +869,17 @@ cudaError_t launch_tc_gemm(const CUtensorMap *tmL, const CUtensorMap *tmR, const
   tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(*tmL, *tmR, p);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm_ragged(const TcSegment *segs, int nseg, int num_tiles,
+                                  const TcGemmParams &p, int num_sms, cudaStream_t s) {
+  TcGemmParams q = p;
+  q.segs = segs;
+  q.nseg = nseg;
+  q.num_tiles = num_tiles;
+  CUtensorMap unused;
+  memset(&unused, 0, sizeof(unused));
+  return launch_tc_gemm(&unused, &unused, q, num_sms, s);
 }
 
 cudaError_t launch_split_terms(const double *src, int nb, int n, int ldp, __nv_bfloat16 *out_l,

@@ -26,7 +26,8 @@ DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16
 SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_sweep",
            "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
            "fa_debug_product", "fa_debug_set_profile", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
-           "fa_launch_count", "fa_launch_count_reset"]
+           "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
+           "fa_batch_solve", "fa_batch_destroy"]
 
 
 class fa_problem_desc(ctypes.Structure):
@@ -76,6 +77,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_debug_set_profile": [dp],
         "fa_product_noalloc": [ctypes.c_int, ctypes.c_int, dp, dp, dp, vp],
         "fa_plan_destroy": [vp],
+        "fa_batch_plan": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(sz)],
+        "fa_batch_bind_workspace": [vp, vp, sz],
+        "fa_batch_solve": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_double)],
+        "fa_batch_destroy": [vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -183,6 +192,35 @@ def fa_launch_count_reset() -> None:
     load_library().fa_launch_count_reset()
 
 
+def fa_batch_plan(ns, flows, Ts, coarse_steps, N, fine_steps, max_iters, tol, dtype, stream_handle):
+    lib = load_library()
+    cnt = len(ns)
+    arr = lambda t, xs: (t * cnt)(*xs)
+    h, ws = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(lib.fa_batch_plan(ctypes.byref(h), cnt, arr(ctypes.c_int, ns), arr(ctypes.c_int, flows),
+                             arr(ctypes.c_double, Ts), arr(ctypes.c_int, coarse_steps), N,
+                             fine_steps, max_iters, float(tol), int(dtype),
+                             ctypes.c_void_p(stream_handle), ctypes.byref(ws)))
+    return h, ws.value
+
+
+def fa_batch_bind_workspace(h, ws_ptr: int, nbytes: int):
+    _check(load_library().fa_batch_bind_workspace(h, ctypes.c_void_p(ws_ptr), nbytes))
+
+
+def fa_batch_solve(h, dAs, dXs, iters, last_dx):
+    cnt = len(dAs)
+    pa = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in dAs])
+    px = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in dXs])
+    return _check(load_library().fa_batch_solve(h, pa, px, iters, last_dx),
+                  allow=(FA_OK, FA_ERR_NOT_CONVERGED))
+
+
+def fa_batch_destroy(h):
+    if _LIB is not None and h:
+        _LIB.fa_batch_destroy(h)
+
+
 # --- convenience wrapper ----------------------------------------------------------------------
 
 class Plan:
@@ -275,6 +313,45 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             fa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent problems (orders, flows, horizons, Euler substeps) solved together."""
+
+    def __init__(self, ns, flows, Ts, coarse_steps, N, fine_steps, max_iters, tol=0.0,
+                 dtype="bf16x6", stream=None):
+        import torch
+
+        self.torch = torch
+        self.ns = list(ns)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle, self.ws_bytes = fa_batch_plan(
+            self.ns, list(flows), list(Ts), list(coarse_steps), N, fine_steps, max_iters, tol,
+            DTYPES[dtype] if isinstance(dtype, str) else int(dtype), self.stream.cuda_stream)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
+        fa_batch_bind_workspace(self.handle, self.ws.data_ptr(), self.ws_bytes)
+
+    def solve(self, As):
+        """As: list of (n_i, n_i) float64 CUDA tensors.  Returns (list of X_i, iters, last_dx, status)."""
+        torch = self.torch
+        As = [a.contiguous() for a in As]
+        Xs = [torch.empty_like(a) for a in As]
+        cnt = len(As)
+        iters = (ctypes.c_int * cnt)()
+        dx = (ctypes.c_double * cnt)()
+        st = fa_batch_solve(self.handle, As, Xs, iters, dx)
+        return Xs, list(iters), list(dx), st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fa_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
