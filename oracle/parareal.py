@@ -116,7 +116,7 @@ def parareal_generic(X0: np.ndarray, N: int,
             G_new.append(g)
             V.append(g + (F_old[n] - G_old[n]))
         ratios = [fro(V[n] - U[n]) / fro(V[n]) for n in range(1, N + 1)]
-        dx = max(ratios)
+        dx = float(np.max(ratios))        # a non-finite slice makes the measure non-finite
         U, G_old = V, G_new
         it += 1
         hist.append(dx)

@@ -85,9 +85,9 @@ def parareal(lam: np.ndarray, flow: int, T: float, N: int, m: int, J: int, K_max
         ratios = [float(np.linalg.norm(v[n] - u[n]) / np.linalg.norm(v[n])) for n in range(1, N + 1)]
         u, g_old = v, g_new
         it += 1
-        hist.append(max(ratios))
+        hist.append(float(np.max(ratios)))
         hist_last.append(ratios[-1])
-        if max(ratios) < tol:
+        if float(np.max(ratios)) < tol:
             break
     return ScalarResult(u=u, iterations=it, dx_history=hist, dx_last_slice=hist_last)
 

@@ -337,3 +337,42 @@ def test_planted_mistakes_are_caught(monkeypatch, mutation):
         monkeypatch.setattr(P, "parareal_generic", generic)
         assert real_generic is not generic
     assert not _pins_pass(), mutation
+
+
+def test_convergence_measure_propagates_non_finite_slices():
+    """A slice whose iterate is not finite makes the stopping test's maximum not finite (the
+    maximum over n of ||dU_n|| / ||U_n||), so a diverging run is never reported converged."""
+    def F(_n, x):
+        return x * np.inf if _n == 2 else 2.0 * x
+    r = P.parareal_generic(np.eye(2), 4, lambda _n, x: x, F, 2, 1e-10)
+    assert not np.isfinite(r.dx_history[0])
+
+
+def test_sign_iteration_solves_the_sylvester_equation():
+    """The block Newton-Schulz sign iteration reaches the eigenbasis solution of X E + E X = R
+    (the plain definition) and the identity P -> I; dropping the P Q P term breaks it."""
+    from oracle import refine as RF
+    sm = inputs.sym_matrix(60, "sqrt", 12)
+    X = S.to_matrix(sm.Q, np.sqrt(sm.lam)) + 1e-3 * inputs.sym_matrix(60, "exp", 13).A
+    X = 0.5 * (X + X.T)
+    R = sm.A - X @ X
+    mu, V = np.linalg.eigh(X)
+    E_exact = V @ ((V.T @ R @ V) / (mu[:, None] + mu[None, :])) @ V.T
+    E, Pm = RF.sylvester_sign(X, R, 16)
+    assert P.rel_fro(E, E_exact) < 1e-11
+    assert np.max(np.abs(Pm - np.eye(60))) < 1e-12
+    assert P.rel_fro(X @ E + E @ X, R) < 1e-11
+    # a scale below lambda_max / sqrt(3) leaves the convergence region
+    E_bad, _ = RF.sylvester_sign(X, R, 16, mu=float(mu[-1]) / 2.0)
+    assert not (P.rel_fro(E_bad, E_exact) < 1e-3)
+
+
+def test_newton_sign_sqrt_matches_eigen_newton():
+    from oracle import refine as RF
+    sm = inputs.sym_matrix(48, "sqrt", 14)
+    X0 = S.to_matrix(sm.Q, closed.scalar_solution(2, sm.lam, 20.0))
+    X0 = X0 + 1e-3 * inputs.sym_matrix(48, "exp", 15).A
+    exact = S.to_matrix(sm.Q, np.sqrt(sm.lam))
+    Xa = RF.newton_sylvester_sqrt(sm.A, X0, 4)
+    Xb = RF.newton_sign_sqrt(sm.A, X0, 4, 18)
+    assert P.rel_fro(Xa, exact) < 1e-10 and P.rel_fro(Xb, exact) < 1e-10
