@@ -91,7 +91,9 @@ typedef struct {
   double tol;         /* stop when max_n ||dU_n||_F / ||U_n||_F < tol (0 = run all K) */
   int fine_dtype;     /* fa_dtype of F */
   int coarse_dtype;   /* fa_dtype of G (FA_F64, or the same BF16 form as F) */
-  int refine_steps;   /* float64 refinement steps on the result (inverse: Newton-Schulz); 0 = none */
+  int refine_steps;   /* refinement steps on the result (inverse: float64 Newton-Schulz; square
+                         root: Newton with the Sylvester equation, see fa_refine); 0 = none */
+  int coarse_kind;    /* fa_coarse_kind of G (FA_COARSE_EULER = the paper's forward Euler) */
 } fa_problem_desc;
 
 typedef struct {
@@ -103,7 +105,19 @@ typedef struct {
   double t_coarse_ms;  /* all coarse sweeps (with correction and norms) */
   double t_refine_ms;  /* refinement */
   double *dx_history;  /* caller-owned host array of max_iters doubles, or NULL */
+  int g_fallback_iter; /* learned G: the iteration after which G was switched to forward Euler
+                          because the convergence measure grew (0 = never) */
+  int coef_fallbacks;  /* learned G: coarse steps whose network output was not finite (Euler used) */
+  int records;         /* pair records written by the recorder (fa_plan_set_recorder) */
 } fa_report;
+
+/* Coarse propagator G.
+ * FA_COARSE_EULER    m forward-Euler substeps per slice (Section 2, Example 1).
+ * FA_COARSE_LEARNED  the learned polynomial step (below; not part of the paper's method):
+ *                    G(X) = X + sum_{j=1..4} c_j dT^j X_[j], X_[j] the j-th Taylor coefficient
+ *                    of the flow through X, c from a small network of cheap features of X.
+ *                    Needs coarse_steps = 1 and the inverse or exponential flow. */
+typedef enum { FA_COARSE_EULER = 0, FA_COARSE_LEARNED = 1 } fa_coarse_kind;
 
 typedef struct fa_plan_s *fa_plan_t;
 
@@ -148,9 +162,18 @@ fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD,
                           double *dUnew, double *dGnew, double *dNorms,
                           const double *dUold);
 
-/* Float64 refinement of dX in place (inverse flow: `refine_steps`
- * Newton-Schulz steps X <- X (2I - A X)).  FA_ERR_UNSUPPORTED for flows
- * without a refinement. */
+/* Refinement of dX in place, `refine_steps` steps (not part of the paper's method; the
+ * mixed-precision forms use it to reach float64-level accuracy):
+ *   inverse flow      Newton-Schulz X <- X (2I - A X), float64 products;
+ *   square-root flow  Newton X <- sym(X) + E with X E + E X = A - X^2: R = A - X^2 in float64,
+ *                     the Sylvester equation solved through the matrix sign function,
+ *                     sign([[X, R], [0, -X]] / mu) = [[I, 2E], [0, -I]] (Roberts 1980, mu the
+ *                     largest eigenvalue of X from a power iteration), by Newton-Schulz sign
+ *                     steps with BF16x6 term products on the tensor cores, stopped two steps
+ *                     after ||I - P^2||_F / sqrt(n) < 1e-6 (at most 60 steps).  Needs an SPD
+ *                     A and an X near A^{1/2}; FA_ERR_NONFINITE if the iteration diverges.
+ * FA_ERR_UNSUPPORTED for the exponential flow.  Synchronises the plan's stream (the sign
+ * iteration reads its stopping measure every step). */
 fa_status fa_refine(fa_plan_t p, double *dX);
 
 /* Whole solve on device buffers: set A, Step 0, up to max_iters parareal
@@ -222,6 +245,99 @@ fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_workspace, size_t bytes)
 fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *dXout, int *iters,
                          double *last_dx);
 fa_status fa_batch_destroy(fa_batch_t b);
+
+/* ---- Learned coarse propagator ----------------------------------------------------------
+ *
+ * Not part of the paper's method: a coarse propagator whose coefficients are learned from
+ * fine-propagator trajectories.  For a state X at slice n (time T_n = n dT, dT = T / N):
+ *
+ *   Taylor terms  inverse flow:     X_[j] = X (B X)^j, B = I - A (the one-slice map is the
+ *                                   Neumann series X (I - dT B X)^{-1});
+ *                 exponential flow: X_[j] = A^j X / j!;
+ *   features      f = [T_n / T, dT, Gershgorin lower and upper bounds of A,
+ *                      h(A) / n, h(X) / n, ||Fl(X)||_F / sqrt(n), ||X||_F / sqrt(n)],
+ *                 h(Y) = (1/8) sum_k z_k^T Y z_k (Hutchinson) over the Rademacher probes
+ *                 z_k[j] = -1 if bit 63 of SplitMix64 output k n + j (seed FA_PROBE_SEED;
+ *                 output c is mix(seed + (c + 1) 0x9E3779B97F4A7C15), Steele, Lea and Flood
+ *                 2014) is set, else +1;
+ *   network       c = W3 g(W2 g(W1 x + b1) + b2) + b3, x = (f - mu) / sd, g = GELU (exact,
+ *                 x Phi(x)); W1: 128 x 8, W2: 128 x 128, W3: 4 x 128 used as BF16 (rounded to
+ *                 nearest even from the float32 blob), everything else float32; float32
+ *                 activations and accumulation;
+ *   update        G(X) = X + sum_j c_j dT^j X_[j]; c = (1, 0, 0, 0) is forward Euler.
+ *
+ * Fallbacks to forward Euler: a slice whose c is not finite uses (1, 0, 0, 0)
+ * (report.coef_fallbacks); if the convergence measure grows from one iteration to the next,
+ * the rest of the solve uses Euler G (G of the current iterate is recomputed with Euler so that
+ * the correction stays consistent; report.g_fallback_iter).
+ *
+ * Parameter blob: FA_MLP_PARAMS float32 values, in order mu[8], sd[8], W1[128][8], b1[128],
+ * W2[128][128], b2[128], W3[4][128], b3[4] (row-major; W maps inputs to outputs as W x).
+ *
+ * Pair record (training data for the pair (X, Y = F(X)), FA_RECORD_DOUBLES float64 values):
+ * [0..7] the features of X; [8..23] M (4 x 4 row-major), M_ab = <Z_a, Z_b>_F; [24..27]
+ * v_a = <Z_a, D>_F; [28] dd = ||D||_F^2; [29..31] zero; with Z_a = dT^a X_[a], D = Y - X.  The
+ * relative residual ||sum_a c_a Z_a - D||^2 / ||D||^2 = (c^T M c - 2 c^T v + dd) / dd is the
+ * training loss of the pair. */
+#define FA_MLP_FEATURES 8
+#define FA_MLP_HIDDEN 128
+#define FA_MLP_COEFS 4
+#define FA_MLP_PARAMS 18196
+#define FA_RECORD_DOUBLES 32
+#define FA_PROBES 8
+#define FA_PROBE_SEED 0x150507959ULL
+
+/* Copy the network blob (device, FA_MLP_PARAMS float32) into the plan (asynchronous).  The plan
+ * must have coarse_kind = FA_COARSE_LEARNED (FA_ERR_ARG otherwise); solves and coarse sweeps
+ * of such a plan fail with FA_ERR_ARG until this has been called. */
+fa_status fa_plan_set_learned(fa_plan_t p, const float *d_params);
+
+/* Coefficients c (device float32 [N][4]) that the plan's last coarse sweep used, per slice. */
+fa_status fa_plan_learned_coefs(fa_plan_t p, float *d_coef);
+
+/* Device scratch (bytes) that fa_learned_records and the recorder need for this plan: four
+ * [N][n][n] float64 arrays plus the stats partials. */
+fa_status fa_learned_records_scratch(fa_plan_t p, size_t *bytes);
+
+/* Pair records of (dU[b], dF[b]) for b = 0..N-1 (device [N][n][n] float64; dF[b] is meant to be
+ * F(dU[b]) from fa_fine_sweep) into d_records (device [N][FA_RECORD_DOUBLES]), feature time
+ * T_b / T = b / N.  The Taylor terms are computed in the plan's fine arithmetic (BF16 term
+ * products on the tensor cores for FA_BF16* fine dtypes, float64 otherwise); the plan's
+ * matrix must be set.  FA_ERR_UNSUPPORTED for the square-root flow. */
+fa_status fa_learned_records(fa_plan_t p, const double *dU, const double *dF, double *d_records,
+                             void *d_scratch, size_t scratch_bytes);
+
+/* Record training pairs during fa_parareal_solve: after every fine sweep, the records of
+ * (U^k_n, F(U^k_n)) for n = 0..N-1 are appended to d_records (device, capacity_pairs records)
+ * while they fit; report.records counts them.  d_scratch as for fa_learned_records.
+ * d_records = NULL switches recording off. */
+fa_status fa_plan_set_recorder(fa_plan_t p, double *d_records, int capacity_pairs,
+                               void *d_scratch, size_t scratch_bytes);
+
+/* Network forward pass: d_coef[b][0..3] (device float32) for `batch` feature rows d_feat
+ * (device float64, row b at d_feat + b * feat_stride; feat_stride >= 8, e.g. FA_RECORD_DOUBLES
+ * to read the features of records).  Non-finite outputs are replaced by (1, 0, 0, 0). */
+fa_status fa_mlp_forward(const float *d_params, int batch, const double *d_feat, int feat_stride,
+                         float *d_coef, void *stream);
+
+/* Device scratch (bytes) of fa_mlp_loss_grad for a batch. */
+fa_status fa_mlp_scratch_bytes(int batch, size_t *bytes);
+
+/* Mean loss over `batch` pair records (device float64 [batch][FA_RECORD_DOUBLES]) into *d_loss
+ * (device float64) and its gradient with respect to the blob into d_grad (device float32
+ * [FA_MLP_PARAMS]; zero for mu and sd), taken at the BF16 weight values the network uses.  The
+ * batch sums of the weight gradients are formed in float64 in sample order (bitwise
+ * reproducible). */
+fa_status fa_mlp_loss_grad(const float *d_params, int batch, const double *d_records,
+                           float *d_grad, double *d_loss, void *d_scratch, size_t scratch_bytes,
+                           void *stream);
+
+/* One Adam step (Kingma and Ba 2015) on W1..b3 of the blob (mu and sd unchanged), float32:
+ * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2; p -= lr (m / (1 - b1^t)) /
+ * (sqrt(v / (1 - b2^t)) + eps).  d_m, d_v: device float32 [FA_MLP_PARAMS], zero before step 1;
+ * `step` = t >= 1. */
+fa_status fa_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
+                      float lr, float beta1, float beta2, float eps, void *stream);
 
 /* Release the plan (not the workspace, which the caller owns). */
 fa_status fa_plan_destroy(fa_plan_t p);

@@ -121,6 +121,35 @@ struct fa_plan_s {
 
   CUtensorMap tmA{}, tmYl[2]{}, tmYr[2]{}, tmPr{}, tmVl[2]{}, tmVr[2]{}, tmPcr{};
 
+  // features (every plan: pair records need them)
+  uint8_t *probes = nullptr;     // n bytes of probe sign bits
+  double *mstats = nullptr;      // Gershgorin lower / upper bound, Hutchinson tr(A)
+  double *spart = nullptr;       // stats partials of one slice
+  bool mstats_valid = false;
+  // learned coarse propagator
+  bool learned = false;          // coarse_kind == FA_COARSE_LEARNED
+  bool learned_active = false;   // cleared by the fallback to Euler inside a solve
+  bool params_set = false;
+  float *mlp = nullptr;          // network blob
+  float *coef = nullptr;         // [N][4] coefficients of the last coarse sweep
+  int *fallbacks = nullptr;      // slices whose network output was not finite
+  double *Rc[4] = {nullptr, nullptr, nullptr, nullptr};   // raw Taylor powers of the coarse state
+  __nv_bfloat16 *Tl[2] = {nullptr, nullptr}, *Tr[2] = {nullptr, nullptr};  // chain operand terms
+  CUtensorMap tmTl[2]{}, tmTr[2]{};
+  // square-root refinement: Newton steps whose Sylvester equations are solved by the
+  // Newton-Schulz sign iteration in BF16x6 term products on the tensor cores
+  double *Xs = nullptr, *Rm = nullptr, *Pm[2] = {nullptr, nullptr}, *Tm = nullptr,
+         *Wm = nullptr, *Vm = nullptr, *Qm = nullptr, *pv = nullptr;
+  __nv_bfloat16 *Lp[2] = {nullptr, nullptr}, *Lt = nullptr, *Lq = nullptr, *Lpq = nullptr;
+  CUtensorMap tmLp[2]{}, tmLt{}, tmLq{}, tmLpq{};
+  size_t strideS = 0;
+  int sign_steps_last = 0;       // sign-iteration steps of the last Newton step (diagnostics)
+  // pair recorder of fa_parareal_solve
+  double *rec = nullptr;
+  int rec_cap = 0, rec_count = 0;
+  void *rec_scratch = nullptr;
+  size_t rec_scratch_bytes = 0;
+
   bool needs_l() const { return d.flow != FA_FLOW_EXP; }  // Y in L form (left factor)
 };
 
@@ -188,6 +217,38 @@ size_t carve(fa_plan_s *p, char *base) {
   } else {
     if (d.flow == FA_FLOW_INV) p->Pc64 = c.take<double>(nn);
   }
+  if (d.flow == FA_FLOW_SQRT && d.refine_steps > 0) {
+    p->Xs = c.take<double>(nn);
+    p->Rm = c.take<double>(nn);
+    p->Pm[0] = c.take<double>(nn);
+    p->Pm[1] = c.take<double>(nn);
+    p->Tm = c.take<double>(nn);
+    p->Wm = c.take<double>(nn);
+    p->Vm = c.take<double>(nn);
+    p->Qm = c.take<double>(nn);
+    p->pv = c.take<double>(2 * static_cast<size_t>(d.n) + 8 + fa::kDevNormBlocks);
+    p->strideS = static_cast<size_t>(d.n) * ldp;
+    p->Lp[0] = c.take<__nv_bfloat16>(3 * p->strideS);
+    p->Lp[1] = c.take<__nv_bfloat16>(3 * p->strideS);
+    p->Lt = c.take<__nv_bfloat16>(3 * p->strideS);
+    p->Lq = c.take<__nv_bfloat16>(3 * p->strideS);
+    p->Lpq = c.take<__nv_bfloat16>(3 * p->strideS);
+  }
+  p->probes = c.take<uint8_t>(static_cast<size_t>(d.n));
+  p->mstats = c.take<double>(8);
+  p->spart = c.take<double>(static_cast<size_t>(fa::stats_blocks(d.n)) * fa::NSTAT);
+  p->coef = c.take<float>(N * FA_MLP_COEFS);
+  p->fallbacks = c.take<int>(4);
+  if (p->learned) {
+    p->mlp = c.take<float>(FA_MLP_PARAMS);
+    for (int j = 0; j < 4; ++j) p->Rc[j] = c.take<double>(nn);
+    if (p->cmixed) {
+      for (int k = 0; k < 2; ++k) {
+        if (d.flow == FA_FLOW_INV) p->Tl[k] = c.take<__nv_bfloat16>(tl * p->strideV);
+        else p->Tr[k] = c.take<__nv_bfloat16>(tr * p->strideV);
+      }
+    }
+  }
   return c.off + 256;
 }
 
@@ -243,6 +304,14 @@ fa_status encode(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nt
 fa_status encode_all(fa_plan_s *p) {
   const int n = p->d.n, ldp = p->ldp, N = p->d.N;
   const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->Lq) {
+    // refinement operands are symmetric (or left factors): one row-major term map serves as
+    // either operand (BM = BN)
+    for (int k = 0; k < 2; ++k) FA_TRY(encode(&p->tmLp[k], p->Lp[k], n, ldp, 1, 3, p->strideS, TC_BM));
+    FA_TRY(encode(&p->tmLt, p->Lt, n, ldp, 1, 3, p->strideS, TC_BM));
+    FA_TRY(encode(&p->tmLq, p->Lq, n, ldp, 1, 3, p->strideS, TC_BM));
+    FA_TRY(encode(&p->tmLpq, p->Lpq, n, ldp, 1, 3, p->strideS, TC_BM));
+  }
   if (p->Aop) FA_TRY(encode(&p->tmA, p->Aop, n, ldp, 1, tl, p->strideA, TC_BM));
   if (p->mixed) {
     for (int k = 0; k < 2; ++k) {
@@ -257,6 +326,10 @@ fa_status encode_all(fa_plan_s *p) {
       if (p->Vl[k]) FA_TRY(encode(&p->tmVl[k], p->Vl[k], n, ldp, 1, tl, p->strideV, TC_BM));
     }
     if (p->Pcr) FA_TRY(encode(&p->tmPcr, p->Pcr, n, ldp, 1, tr, p->strideV, TC_BN));
+    for (int k = 0; k < 2; ++k) {
+      if (p->Tl[k]) FA_TRY(encode(&p->tmTl[k], p->Tl[k], n, ldp, 1, tl, p->strideV, TC_BM));
+      if (p->Tr[k]) FA_TRY(encode(&p->tmTr[k], p->Tr[k], n, ldp, 1, tr, p->strideV, TC_BN));
+    }
   }
   return FA_OK;
 }
@@ -387,20 +460,60 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
 
 // ---- coarse sweep ----------------------------------------------------------------------------
 
-fa_status coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *Unew, double *Gout,
-                       double *norms, const double *Uold) {
+// The product(s) of one forward-Euler substep on the single-slice coarse state vin (operand
+// terms in Vl/Vr[cur] when the coarse arithmetic is mixed), with the Euler epilogue e.
+fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
   const fa_problem_desc &d = p->d;
-  const int n = d.n, N = d.N, m = d.coarse_steps;
+  const int tr = p->ps.terms_r;
+  if (p->cmixed) {
+    e.a_hi = p->a_hi;
+    e.a_lo = p->a_lo;
+    if (d.flow == FA_FLOW_EXP) {
+      FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+    } else if (d.flow == FA_FLOW_SQRT) {
+      FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+    } else {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out_r = p->Pcr;
+      e1.terms_r = tr;
+      e1.term_stride_r = p->strideV;
+      FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e1)));
+      FA_TRY(tc(p, p->tmVl[cur], p->tmPcr, tc_params(p, 1, 0, 0, e)));
+    }
+  } else {
+    e.a64 = p->A64;
+    if (d.flow == FA_FLOW_EXP) {
+      FA_TRY(f64(p, p->A64, 0, vin, 0, 1, e));
+    } else if (d.flow == FA_FLOW_SQRT) {
+      FA_TRY(f64(p, vin, 0, vin, 0, 1, e));
+    } else {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out64 = p->Pc64;
+      FA_TRY(f64(p, p->B64, 0, vin, 0, 1, e1));
+      FA_TRY(f64(p, vin, 0, p->Pc64, 0, 1, e));
+    }
+  }
+  return FA_OK;
+}
+
+// BF16 operand terms of a single-slice coarse state into Vl/Vr[k].
+fa_status split_coarse(fa_plan_s *p, const double *v, int k) {
+  FA_CUDA(fa::launch_split_terms(v, 1, p->d.n, p->ldp, p->Vl[k], p->needs_l() ? p->ps.terms_l : 0,
+                                 p->strideV, p->Vr[k], p->ps.terms_r, p->strideV, 0, p->stream));
+  return FA_OK;
+}
+
+fa_status euler_coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *Unew,
+                             double *Gout, double *norms, const double *Uold) {
+  const fa_problem_desc &d = p->d;
+  const int N = d.N, m = d.coarse_steps;
   const size_t nn = p->nn;
   const double dt = d.T / static_cast<double>(N) / static_cast<double>(m);
   const int tl = p->ps.terms_l, tr = p->ps.terms_r;
-  if (Unew != U0)
-    FA_CUDA(cudaMemcpyAsync(Unew, U0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   int cur = 0;
-  if (p->cmixed) {
-    FA_CUDA(fa::launch_split_terms(U0, 1, n, p->ldp, p->Vl[0], p->needs_l() ? tl : 0,
-                                   p->strideV, p->Vr[0], tr, p->strideV, 0, p->stream));
-  }
+  if (p->cmixed) FA_TRY(split_coarse(p, U0, 0));
   const int tiles = p->part_tiles;
   for (int s = 0; s < N; ++s) {
     for (int sub = 0; sub < m; ++sub) {
@@ -420,44 +533,283 @@ fa_status coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *
         e.norm_part = p->part + static_cast<size_t>(s) * tiles * 2;
       }
       if (p->cmixed) {
-        e.a_hi = p->a_hi;
-        e.a_lo = p->a_lo;
         e.out_r = p->Vr[cur ^ 1];
         e.out_l = p->Vl[cur ^ 1];
         e.terms_r = tr;
         e.terms_l = p->needs_l() ? tl : 0;
         e.term_stride_r = e.term_stride_l = p->strideV;
-        if (d.flow == FA_FLOW_EXP) {
-          FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
-        } else if (d.flow == FA_FLOW_SQRT) {
-          FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
-        } else {
-          EpiParams e1 = base_epi(p);
-          e1.mode = fa::EPI_PROD;
-          e1.out_r = p->Pcr;
-          e1.terms_r = tr;
-          e1.term_stride_r = p->strideV;
-          FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e1)));
-          FA_TRY(tc(p, p->tmVl[cur], p->tmPcr, tc_params(p, 1, 0, 0, e)));
-        }
-        cur ^= 1;
-      } else {
-        e.a64 = p->A64;
-        if (d.flow == FA_FLOW_EXP) {
-          FA_TRY(f64(p, p->A64, 0, vin, 0, 1, e));
-        } else if (d.flow == FA_FLOW_SQRT) {
-          FA_TRY(f64(p, vin, 0, vin, 0, 1, e));
-        } else {
-          EpiParams e1 = base_epi(p);
-          e1.mode = fa::EPI_PROD;
-          e1.out64 = p->Pc64;
-          FA_TRY(f64(p, p->B64, 0, vin, 0, 1, e1));
-          FA_TRY(f64(p, vin, 0, p->Pc64, 0, 1, e));
-        }
       }
+      FA_TRY(euler_gemm(p, cur, vin, e));
+      if (p->cmixed) cur ^= 1;
     }
   }
-  if (norms && Uold) FA_CUDA(fa::launch_reduce_norms(p->part, N, tiles, norms, p->stream));
+  return FA_OK;
+}
+
+// Gershgorin bounds and Hutchinson tr(A) of the plan's matrix (once per matrix).
+fa_status ensure_mstats(fa_plan_s *p) {
+  if (p->mstats_valid) return FA_OK;
+  fa::StatsArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = p->d.n;
+  a.rows_per_block = fa::stats_rows_per_block(a.n);
+  a.X = p->A64;
+  a.probes = p->probes;
+  a.gersh = 1;
+  a.part = p->spart;
+  FA_CUDA(fa::launch_stats(a, 1, p->stream));
+  FA_CUDA(fa::launch_matrix_stats(p->spart, a.n, p->mstats, p->stream));
+  p->mstats_valid = true;
+  return FA_OK;
+}
+
+// Taylor scale s_j = dT^j kappa_j of the raw power R_j (kappa_j = 1 for the inverse flow,
+// 1 / j! for the exponential flow).
+fa::RecordScale taylor_scale(const fa_plan_s *p) {
+  fa::RecordScale sc;
+  const double dT = p->d.T / static_cast<double>(p->d.N);
+  double pw = 1.0, fact = 1.0;
+  for (int j = 0; j < 4; ++j) {
+    pw *= dT;
+    fact *= (j + 1);
+    sc.s[j] = p->d.flow == FA_FLOW_EXP ? pw / fact : pw;
+  }
+  return sc;
+}
+
+// Raw Taylor powers R_1..R_4 of the single-slice coarse state vin into Rc (inverse flow:
+// P = B V, R_1 = V P, R_{j+1} = R_j P; exponential flow: R_1 = A V, R_{j+1} = A R_j).
+fa_status coarse_taylor(fa_plan_s *p, int cur, const double *vin) {
+  const bool inv = p->d.flow == FA_FLOW_INV;
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->cmixed) {
+    if (inv) {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out_r = p->Pcr;
+      e1.terms_r = tr;
+      e1.term_stride_r = p->strideV;
+      FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e1)));
+    }
+    for (int j = 0; j < 4; ++j) {
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_TAYLOR;
+      e.out64 = p->Rc[j];
+      if (j < 3) {
+        if (inv) {
+          e.out_l = p->Tl[j & 1];
+          e.terms_l = tl;
+          e.term_stride_l = p->strideV;
+        } else {
+          e.out_r = p->Tr[j & 1];
+          e.terms_r = tr;
+          e.term_stride_r = p->strideV;
+        }
+      }
+      if (inv) {
+        const CUtensorMap &L = j == 0 ? p->tmVl[cur] : p->tmTl[(j - 1) & 1];
+        FA_TRY(tc(p, L, p->tmPcr, tc_params(p, 1, 0, 0, e)));
+      } else {
+        const CUtensorMap &R = j == 0 ? p->tmVr[cur] : p->tmTr[(j - 1) & 1];
+        FA_TRY(tc(p, p->tmA, R, tc_params(p, 1, 0, 0, e)));
+      }
+    }
+  } else {
+    if (inv) {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out64 = p->Pc64;
+      FA_TRY(f64(p, p->B64, 0, vin, 0, 1, e1));
+    }
+    for (int j = 0; j < 4; ++j) {
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_TAYLOR;
+      e.out64 = p->Rc[j];
+      const double *src = j == 0 ? vin : p->Rc[j - 1];
+      if (inv) FA_TRY(f64(p, src, 0, p->Pc64, 0, 1, e));
+      else FA_TRY(f64(p, p->A64, 0, src, 0, 1, e));
+    }
+  }
+  return FA_OK;
+}
+
+// Coarse sweep with the learned polynomial step: per slice, the Taylor powers, the stats of
+// the state, the network (one block) and the update with correction and norms.
+fa_status learned_coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *Unew,
+                               double *Gout, double *norms, const double *Uold) {
+  const fa_problem_desc &d = p->d;
+  if (!p->params_set) return set_err(FA_ERR_ARG, "fa_plan_set_learned has not been called");
+  FA_TRY(ensure_mstats(p));
+  const int n = d.n, N = d.N;
+  const size_t nn = p->nn;
+  const double dT = d.T / static_cast<double>(N);
+  const fa::RecordScale sc = taylor_scale(p);
+  const int tiles = p->part_tiles;
+  int cur = 0;
+  if (p->cmixed) FA_TRY(split_coarse(p, U0, 0));
+  for (int s = 0; s < N; ++s) {
+    const double *vin = Unew + static_cast<size_t>(s) * nn;
+    double *vout = Unew + static_cast<size_t>(s + 1) * nn;
+    FA_TRY(coarse_taylor(p, cur, vin));
+    fa::StatsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.rows_per_block = fa::stats_rows_per_block(n);
+    a.X = vin;
+    a.R[0] = p->Rc[0];
+    a.nR = 1;
+    a.probes = p->probes;
+    a.part = p->spart;
+    FA_CUDA(fa::launch_stats(a, 1, p->stream));
+    float *cf = p->coef + static_cast<size_t>(s) * FA_MLP_COEFS;
+    FA_CUDA(fa::launch_coarse_coef(p->mlp, p->spart, n, s, N, dT, p->mstats, cf, p->fallbacks,
+                                   p->stream));
+    fa::CombineArgs c;
+    memset(&c, 0, sizeof(c));
+    c.n = n;
+    c.v_in = vin;
+    for (int j = 0; j < 4; ++j) {
+      c.R[j] = p->Rc[j];
+      c.scale[j] = sc.s[j];
+    }
+    c.coef = cf;
+    c.d_in = D ? D + static_cast<size_t>(s) * nn : nullptr;
+    const bool nrm = norms && Uold;
+    c.u_old = nrm ? Uold + static_cast<size_t>(s + 1) * nn : nullptr;
+    c.g_out = Gout + static_cast<size_t>(s) * nn;
+    c.v_out = vout;
+    c.norm_part = nrm ? p->part + static_cast<size_t>(s) * tiles * 2 : nullptr;
+    FA_CUDA(fa::launch_combine(c, tiles, p->stream));
+    if (p->cmixed && s + 1 < N) {
+      FA_TRY(split_coarse(p, vout, cur ^ 1));
+      cur ^= 1;
+    }
+  }
+  return FA_OK;
+}
+
+fa_status coarse_sweep(fa_plan_s *p, const double *U0, const double *D, double *Unew, double *Gout,
+                       double *norms, const double *Uold) {
+  const fa_problem_desc &d = p->d;
+  if (Unew != U0)
+    FA_CUDA(cudaMemcpyAsync(Unew, U0, p->nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  if (p->learned_active) FA_TRY(learned_coarse_sweep(p, U0, D, Unew, Gout, norms, Uold));
+  else FA_TRY(euler_coarse_sweep(p, U0, D, Unew, Gout, norms, Uold));
+  if (norms && Uold) FA_CUDA(fa::launch_reduce_norms(p->part, d.N, p->part_tiles, norms, p->stream));
+  return FA_OK;
+}
+
+// Forward-Euler G of every slice of U into Gout (independent steps; the fallback of the learned
+// propagator recomputes the cached G(U^k_n) with it).
+fa_status euler_all(fa_plan_s *p, const double *U, double *Gout) {
+  const fa_problem_desc &d = p->d;
+  const size_t nn = p->nn;
+  const double dt = d.T / static_cast<double>(d.N);
+  for (int s = 0; s < d.N; ++s) {
+    const double *vin = U + static_cast<size_t>(s) * nn;
+    if (p->cmixed) FA_TRY(split_coarse(p, vin, 0));
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_EULER;
+    e.dt = dt;
+    e.v_in = vin;
+    e.v_out = Gout + static_cast<size_t>(s) * nn;
+    e.g_out = Gout + static_cast<size_t>(s) * nn;
+    e.euler_last = 1;
+    FA_TRY(euler_gemm(p, 0, vin, e));
+  }
+  return FA_OK;
+}
+
+// ---- pair records ------------------------------------------------------------------------------
+
+size_t records_scratch_bytes(const fa_plan_s *p) {
+  const size_t N = static_cast<size_t>(p->d.N);
+  return 4 * (N * p->nn * sizeof(double) + 256) +
+         N * fa::stats_blocks(p->d.n) * fa::NSTAT * sizeof(double) + 256;
+}
+
+// Records of the pairs (U_b, F_b) (F_b = F[b] + G[b] when G is given) for b = 0..N-1, Taylor
+// powers in the fine arithmetic (the fine sweep's operand buffers serve as chain storage).
+fa_status records(fa_plan_s *p, const double *U, const double *F, const double *G, double *out,
+                  void *scratch, size_t scratch_bytes) {
+  const fa_problem_desc &d = p->d;
+  if (d.flow == FA_FLOW_SQRT)
+    return set_err(FA_ERR_UNSUPPORTED, "pair records are implemented for the inverse and exponential flows");
+  if (!scratch || scratch_bytes < records_scratch_bytes(p))
+    return set_err(FA_ERR_WORKSPACE, "records scratch of %zu bytes < %zu needed", scratch_bytes,
+                   records_scratch_bytes(p));
+  FA_TRY(ensure_mstats(p));
+  const int n = d.n, N = d.N;
+  const size_t nn = p->nn;
+  Carver c{static_cast<char *>(scratch)};
+  double *R[4];
+  for (int j = 0; j < 4; ++j) R[j] = c.take<double>(N * nn);
+  double *part = c.take<double>(static_cast<size_t>(N) * fa::stats_blocks(n) * fa::NSTAT);
+  const bool inv = d.flow == FA_FLOW_INV;
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->mixed) {
+    FA_CUDA(fa::launch_split_terms(U, N, n, p->ldp, inv ? p->Yl[0] : nullptr, inv ? tl : 0,
+                                   p->strideY, p->Yr[0], tr, p->strideY, 0, p->stream));
+    if (inv) {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out_r = p->Pr;
+      e1.terms_r = tr;
+      e1.term_stride_r = p->strideY;
+      FA_TRY(tc(p, p->tmA, p->tmYr[0], tc_params(p, N, 0, 1, e1)));
+    }
+    for (int j = 0; j < 4; ++j) {
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_TAYLOR;
+      e.out64 = R[j];
+      const int src = j & 1, dst = (j + 1) & 1;
+      if (j < 3) {
+        if (inv) {
+          e.out_l = p->Yl[dst];
+          e.terms_l = tl;
+          e.term_stride_l = p->strideY;
+        } else {
+          e.out_r = p->Yr[dst];
+          e.terms_r = tr;
+          e.term_stride_r = p->strideY;
+        }
+      }
+      if (inv) FA_TRY(tc(p, p->tmYl[src], p->tmPr, tc_params(p, N, 1, 1, e)));
+      else FA_TRY(tc(p, p->tmA, p->tmYr[src], tc_params(p, N, 0, 1, e)));
+    }
+  } else {
+    if (inv) {
+      EpiParams e1 = base_epi(p);
+      e1.mode = fa::EPI_PROD;
+      e1.out64 = p->P64;
+      FA_TRY(f64(p, p->B64, 0, U, nn, N, e1));
+    }
+    for (int j = 0; j < 4; ++j) {
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_TAYLOR;
+      e.out64 = R[j];
+      const double *src = j == 0 ? U : R[j - 1];
+      if (inv) FA_TRY(f64(p, src, nn, p->P64, nn, N, e));
+      else FA_TRY(f64(p, p->A64, 0, src, nn, N, e));
+    }
+  }
+  fa::StatsArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.rows_per_block = fa::stats_rows_per_block(n);
+  a.X = U;
+  a.x_stride = nn;
+  a.F = F;
+  a.G = G;
+  a.f_stride = nn;
+  for (int j = 0; j < 4; ++j) a.R[j] = R[j];
+  a.r_stride = nn;
+  a.nR = 4;
+  a.probes = p->probes;
+  a.part = part;
+  FA_CUDA(fa::launch_stats(a, N, p->stream));
+  FA_CUDA(fa::launch_records(part, N, n, N, 0, d.T / N, taylor_scale(p), p->mstats, out,
+                             p->stream));
   return FA_OK;
 }
 
@@ -471,11 +823,94 @@ fa_status read_err(fa_plan_s *p) {
   return FA_OK;
 }
 
+// Square-root refinement: Newton steps X <- X + E with X E + E X = A - X^2.  Per step: X is
+// symmetrised, R = A - X^2 in float64, mu = the largest eigenvalue of X (power iteration), and
+// the Sylvester equation is solved through sign([[X, R], [0, -X]] / mu) = [[I, 2E], [0, -I]]
+// (Roberts 1980) by the Newton-Schulz sign iteration on the blocks,
+//     T = 3I - P^2,  Q <- (T Q + Q T - 3Q + P Q P) / 2,  P <- P T / 2,
+// from P = X / mu, Q = R / mu, with every product a BF16x6 term product on the tensor cores
+// (the products' epilogues write the operand terms of the next products).  The iteration stops
+// two steps after ||I - P^2||_F / sqrt(n) < 1e-6.
+fa_status refine_sqrt(fa_plan_s *p, double *X) {
+  const int n = p->d.n;
+  const fa::PairSet ps6 = fa::pair_set(FA_BF16X6);
+  double *v = p->pv, *y = v + n, *lam = y + n, *dn = lam + 1, *parts = lam + 8;
+  auto prod = [&](const CUtensorMap &L, const CUtensorMap &R, double alpha, double beta,
+                  double *out64, __nv_bfloat16 *terms) -> fa_status {
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_STORE;
+    e.alpha = alpha;
+    e.beta = beta;
+    e.store_out = out64;
+    if (terms) {
+      e.out_l = terms;
+      e.terms_l = 3;
+      e.term_stride_l = p->strideS;
+    }
+    TcGemmParams g = fa::tc_launch_params(n, 1, 0, 0, ps6);
+    g.epi = e;
+    return tc(p, L, R, g);
+  };
+  auto split = [&](const double *src, __nv_bfloat16 *dst) -> fa_status {
+    FA_CUDA(fa::launch_split_terms(src, 1, n, p->ldp, dst, 3, p->strideS, nullptr, 0, 0, 0,
+                                   p->stream));
+    return FA_OK;
+  };
+  for (int st = 0; st < p->d.refine_steps; ++st) {
+    FA_CUDA(fa::launch_sym_combine(n, 1.0, X, 0.0, nullptr, 0.0, nullptr, p->Xs, p->stream));
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_STORE;
+    e.alpha = -1.0;
+    e.beta = 0.0;
+    e.store_add = p->A64;
+    e.store_out = p->Rm;
+    FA_TRY(f64(p, p->Xs, 0, p->Xs, 0, 1, e));                       // R = A - X^2
+    FA_CUDA(fa::launch_fill(v, n, 1.0 / std::sqrt(static_cast<double>(n)), p->stream));
+    for (int it = 0; it < 40; ++it) FA_CUDA(fa::launch_power_step(p->Xs, n, v, y, lam, p->stream));
+    double mu = 0.0;
+    FA_CUDA(cudaMemcpyAsync(&mu, lam, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    if (!(mu > 0.0) || !std::isfinite(mu))
+      return set_err(FA_ERR_NONFINITE, "square-root refinement: no positive spectral scale");
+    FA_CUDA(fa::launch_sym_combine(n, 1.0 / mu, p->Xs, 0.0, nullptr, 0.0, nullptr, p->Pm[0],
+                                   p->stream));
+    FA_TRY(split(p->Pm[0], p->Lp[0]));
+    FA_CUDA(fa::launch_sym_combine(n, 1.0 / mu, p->Rm, 0.0, nullptr, 0.0, nullptr, p->Qm,
+                                   p->stream));
+    FA_TRY(split(p->Qm, p->Lq));
+    int cur = 0, extra = -1, k = 0;
+    const double stop = 1e-12 * n;                     // ||I - P^2||_F^2 < (1e-6)^2 n
+    for (; k < 60; ++k) {
+      FA_TRY(prod(p->tmLp[cur], p->tmLp[cur], -1.0, 3.0, p->Tm, p->Lt));          // T
+      FA_TRY(prod(p->tmLp[cur], p->tmLt, 0.5, 0.0, p->Pm[cur ^ 1], p->Lp[cur ^ 1]));  // P'
+      FA_TRY(prod(p->tmLt, p->tmLq, 1.0, 0.0, p->Wm, nullptr));                   // W = T Q
+      FA_TRY(prod(p->tmLp[cur], p->tmLq, 1.0, 0.0, nullptr, p->Lpq));             // P Q
+      FA_TRY(prod(p->tmLpq, p->tmLp[cur], 1.0, 0.0, p->Vm, nullptr));             // V = P Q P
+      FA_CUDA(fa::launch_sym_combine(n, 1.0, p->Wm, -1.5, p->Qm, 0.5, p->Vm, p->Qm, p->stream));
+      FA_TRY(split(p->Qm, p->Lq));
+      cur ^= 1;
+      FA_CUDA(fa::launch_dev_norm(p->Tm, n, 2.0, parts, dn, p->stream));
+      double dev = 0.0;
+      FA_CUDA(cudaMemcpyAsync(&dev, dn, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      FA_CUDA(cudaStreamSynchronize(p->stream));
+      if (!std::isfinite(dev))
+        return set_err(FA_ERR_NONFINITE, "square-root refinement: sign iteration diverged");
+      if (extra < 0 && dev < stop) extra = 2;
+      if (extra == 0) break;
+      if (extra > 0) --extra;
+    }
+    p->sign_steps_last = k + 1;
+    FA_CUDA(fa::launch_sym_combine(n, 1.0, p->Xs, 0.0, nullptr, 0.5, p->Qm, X, p->stream));
+  }
+  return FA_OK;
+}
+
 fa_status refine(fa_plan_s *p, double *X) {
   const fa_problem_desc &d = p->d;
   if (d.refine_steps <= 0) return FA_OK;
+  if (d.flow == FA_FLOW_SQRT) return refine_sqrt(p, X);
   if (d.flow != FA_FLOW_INV)
-    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+    return set_err(FA_ERR_UNSUPPORTED, "the exponential flow has no refinement");
   for (int s = 0; s < d.refine_steps; ++s) {
     // T = 2I - A X ; X <- X T  (Newton-Schulz)
     EpiParams e = base_epi(p);
@@ -729,6 +1164,15 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   if (d->coarse_dtype != FA_F64 && d->coarse_dtype != d->fine_dtype)
     return set_err(FA_ERR_ARG, "coarse dtype must be FA_F64 or the fine dtype");
   if (d->refine_steps < 0) return set_err(FA_ERR_ARG, "refine_steps must be >= 0");
+  if (d->coarse_kind != FA_COARSE_EULER && d->coarse_kind != FA_COARSE_LEARNED)
+    return set_err(FA_ERR_ARG, "unknown coarse kind %d", d->coarse_kind);
+  if (d->coarse_kind == FA_COARSE_LEARNED) {
+    if (d->flow == FA_FLOW_SQRT)
+      return set_err(FA_ERR_UNSUPPORTED,
+                     "the learned coarse propagator supports the inverse and exponential flows");
+    if (d->coarse_steps != 1)
+      return set_err(FA_ERR_ARG, "the learned coarse propagator takes one step per slice");
+  }
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return set_err(FA_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
@@ -750,6 +1194,8 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   p->ps = fa::pair_set(p->mixed ? d->fine_dtype : d->coarse_dtype);
   p->ldp = (d->n + 7) / 8 * 8;
   p->nn = static_cast<size_t>(d->n) * d->n;
+  p->learned = d->coarse_kind == FA_COARSE_LEARNED;
+  p->learned_active = p->learned;
   p->part_tiles = p->cmixed ? ((d->n + TC_BM - 1) / TC_BM) * ((d->n + TC_BN - 1) / TC_BN)
                             : fa::f64_tiles_per_slice(d->n, 1);
   p->ws_need = carve(p, nullptr);
@@ -768,8 +1214,12 @@ fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
   p->ws = static_cast<char *>(ws);
   carve(p, p->ws);
   p->matrix_set = false;
+  p->mstats_valid = false;
+  p->params_set = false;
   FA_TRY(encode_all(p));
   FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  FA_CUDA(cudaMemsetAsync(p->fallbacks, 0, sizeof(int), p->stream));
+  FA_CUDA(fa::launch_probes(p->d.n, p->probes, p->stream));
   return FA_OK;
 }
 
@@ -781,6 +1231,7 @@ fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA) {
   if (dA != p->A64)
     FA_CUDA(cudaMemcpyAsync(p->A64, dA, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   FA_CUDA(fa::launch_check_finite(p->A64, nn, p->err, p->stream));
+  p->mstats_valid = false;
   if (p->B64) FA_CUDA(fa::launch_i_minus(p->A64, n, p->B64, p->stream));
   if (p->mixed || p->cmixed) {
     const int tl = p->ps.terms_l;
@@ -814,8 +1265,8 @@ fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD, doub
 fa_status fa_refine(fa_plan_t p, double *dX) {
   FA_TRY(check_ready(p, true));
   if (!dX) return set_err(FA_ERR_ARG, "null pointer");
-  if (p->d.flow != FA_FLOW_INV)
-    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+  if (p->d.flow == FA_FLOW_EXP)
+    return set_err(FA_ERR_UNSUPPORTED, "the exponential flow has no refinement");
   return refine(p, dX);
 }
 
@@ -823,8 +1274,8 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
                             fa_report *r) {
   FA_TRY(check_ready(p, false));
   if (!dA || !dXout) return set_err(FA_ERR_ARG, "null pointer");
-  if (p->d.refine_steps > 0 && p->d.flow != FA_FLOW_INV)
-    return set_err(FA_ERR_UNSUPPORTED, "refinement is implemented for the inverse flow only");
+  if (p->d.refine_steps > 0 && p->d.flow == FA_FLOW_EXP)
+    return set_err(FA_ERR_UNSUPPORTED, "the exponential flow has no refinement");
   const fa_problem_desc &d = p->d;
   const size_t nn = p->nn;
   cudaEvent_t ev[4];
@@ -835,7 +1286,13 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
       for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
     }
   } guard{ev};
+  if (p->learned && !p->params_set)
+    return set_err(FA_ERR_ARG, "fa_plan_set_learned has not been called");
   FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  FA_CUDA(cudaMemsetAsync(p->fallbacks, 0, sizeof(int), p->stream));
+  p->learned_active = p->learned;
+  p->rec_count = 0;
+  int g_fallback_iter = 0;
   FA_CUDA(cudaEventRecord(ev[0], p->stream));
   FA_TRY(fa_plan_set_matrix(p, dA));
   if (dX0) {
@@ -852,12 +1309,18 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
   double t_init = ms, t_fine = 0.0, t_coarse = 0.0, t_ref = 0.0;
   int iters = 0;
   bool converged = false;
-  double dx = INFINITY;
+  double dx = INFINITY, prev_dx = INFINITY;
   fa_status st = FA_OK;
   for (int k = 0; k < d.max_iters; ++k) {
     // Step k+1: the fine propagator on every slice at once, D_n = F(U^k_n) - G(U^k_n) ...
     FA_CUDA(cudaEventRecord(ev[1], p->stream));
     FA_TRY(fine_sweep(p, p->U, p->D, p->Gold));
+    if (p->rec && p->rec_count + d.N <= p->rec_cap) {
+      // training pairs (U^k_n, F(U^k_n)), F(U^k_n) = D_n + G(U^k_n)
+      FA_TRY(records(p, p->U, p->D, p->Gold, p->rec + static_cast<size_t>(p->rec_count) * FA_RECORD_DOUBLES,
+                     p->rec_scratch, p->rec_scratch_bytes));
+      p->rec_count += d.N;
+    }
     FA_CUDA(cudaEventRecord(ev[2], p->stream));
     // ... then the sequential correction U^{k+1}_{n+1} = G(U^{k+1}_n) + D_n (eq. eqStepk+1).
     FA_TRY(coarse_sweep(p, p->U, p->D, p->U, p->Gnew, p->norms, p->U));
@@ -882,6 +1345,14 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
       converged = true;
       break;
     }
+    if (p->learned_active && k > 0 && dx > prev_dx) {
+      // Fallback: the rest of the solve runs with Euler G; G(U^k_n) is recomputed with it so
+      // that the next correction F(U^k_n) - G(U^k_n) uses one propagator.
+      p->learned_active = false;
+      g_fallback_iter = k + 1;
+      FA_TRY(euler_all(p, p->U, p->Gold));
+    }
+    prev_dx = dx;
   }
   FA_CUDA(cudaMemcpyAsync(dXout, p->U + static_cast<size_t>(d.N) * nn, nn * sizeof(double),
                           cudaMemcpyDeviceToDevice, p->stream));
@@ -893,8 +1364,15 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
     FA_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
     t_ref = ms;
   }
+  p->learned_active = p->learned;
   fa_status es = read_err(p);
+  int coef_fb = 0;
+  FA_CUDA(cudaMemcpyAsync(&coef_fb, p->fallbacks, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaStreamSynchronize(p->stream));
   if (r) {
+    r->g_fallback_iter = g_fallback_iter;
+    r->coef_fallbacks = coef_fb;
+    r->records = p->rec_count;
     r->iters = iters;
     r->converged = converged ? 1 : 0;
     r->last_dx = dx;
@@ -950,6 +1428,101 @@ fa_status fa_debug_set_profile(unsigned long long *d_counters) {
   return FA_OK;
 }
 
+
+fa_status fa_plan_set_learned(fa_plan_t p, const float *d_params) {
+  FA_TRY(check_ready(p, false));
+  if (!p->learned) return set_err(FA_ERR_ARG, "the plan's coarse kind is not FA_COARSE_LEARNED");
+  if (!d_params) return set_err(FA_ERR_ARG, "null parameter blob");
+  FA_CUDA(cudaMemcpyAsync(p->mlp, d_params, FA_MLP_PARAMS * sizeof(float),
+                          cudaMemcpyDeviceToDevice, p->stream));
+  p->params_set = true;
+  return FA_OK;
+}
+
+fa_status fa_plan_learned_coefs(fa_plan_t p, float *d_coef) {
+  FA_TRY(check_ready(p, false));
+  if (!d_coef) return set_err(FA_ERR_ARG, "null pointer");
+  FA_CUDA(cudaMemcpyAsync(d_coef, p->coef, static_cast<size_t>(p->d.N) * FA_MLP_COEFS * sizeof(float),
+                          cudaMemcpyDeviceToDevice, p->stream));
+  return FA_OK;
+}
+
+fa_status fa_learned_records_scratch(fa_plan_t p, size_t *bytes) {
+  if (!p || !bytes) return set_err(FA_ERR_ARG, "null argument");
+  *bytes = records_scratch_bytes(p);
+  return FA_OK;
+}
+
+fa_status fa_learned_records(fa_plan_t p, const double *dU, const double *dF, double *d_records,
+                             void *d_scratch, size_t scratch_bytes) {
+  FA_TRY(check_ready(p, true));
+  if (!dU || !dF || !d_records) return set_err(FA_ERR_ARG, "null pointer");
+  return records(p, dU, dF, nullptr, d_records, d_scratch, scratch_bytes);
+}
+
+fa_status fa_plan_set_recorder(fa_plan_t p, double *d_records, int capacity_pairs, void *d_scratch,
+                               size_t scratch_bytes) {
+  FA_TRY(check_ready(p, false));
+  if (!d_records) {
+    p->rec = nullptr;
+    p->rec_cap = 0;
+    return FA_OK;
+  }
+  if (p->d.flow == FA_FLOW_SQRT)
+    return set_err(FA_ERR_UNSUPPORTED, "pair records are implemented for the inverse and exponential flows");
+  if (capacity_pairs < 0) return set_err(FA_ERR_ARG, "capacity must be >= 0");
+  if (!d_scratch || scratch_bytes < records_scratch_bytes(p))
+    return set_err(FA_ERR_WORKSPACE, "records scratch of %zu bytes < %zu needed", scratch_bytes,
+                   records_scratch_bytes(p));
+  p->rec = d_records;
+  p->rec_cap = capacity_pairs;
+  p->rec_scratch = d_scratch;
+  p->rec_scratch_bytes = scratch_bytes;
+  return FA_OK;
+}
+
+fa_status fa_mlp_forward(const float *d_params, int batch, const double *d_feat, int feat_stride,
+                         float *d_coef, void *stream) {
+  if (!d_params || !d_feat || !d_coef) return set_err(FA_ERR_ARG, "null pointer");
+  if (batch < 0 || feat_stride < FA_MLP_FEATURES) return set_err(FA_ERR_ARG, "bad batch or stride");
+  if (batch == 0) return FA_OK;
+  FA_CUDA(fa::launch_mlp_forward(d_params, batch, d_feat, feat_stride, d_coef, nullptr,
+                                 static_cast<cudaStream_t>(stream)));
+  return FA_OK;
+}
+
+fa_status fa_mlp_scratch_bytes(int batch, size_t *bytes) {
+  if (batch < 1 || !bytes) return set_err(FA_ERR_ARG, "batch must be >= 1");
+  *bytes = fa::mlp_train_scratch_bytes(batch);
+  return FA_OK;
+}
+
+fa_status fa_mlp_loss_grad(const float *d_params, int batch, const double *d_records,
+                           float *d_grad, double *d_loss, void *d_scratch, size_t scratch_bytes,
+                           void *stream) {
+  if (!d_params || !d_records || !d_grad || !d_loss || !d_scratch)
+    return set_err(FA_ERR_ARG, "null pointer");
+  if (batch < 1) return set_err(FA_ERR_ARG, "batch must be >= 1");
+  if (scratch_bytes < fa::mlp_train_scratch_bytes(batch))
+    return set_err(FA_ERR_WORKSPACE, "scratch of %zu bytes < %zu needed", scratch_bytes,
+                   fa::mlp_train_scratch_bytes(batch));
+  if (reinterpret_cast<uintptr_t>(d_scratch) & 255)
+    return set_err(FA_ERR_WORKSPACE, "scratch must be 256-byte aligned");
+  FA_CUDA(fa::launch_mlp_loss_grad(d_params, batch, d_records, d_scratch, d_grad, d_loss,
+                                   static_cast<cudaStream_t>(stream)));
+  return FA_OK;
+}
+
+fa_status fa_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
+                      float lr, float beta1, float beta2, float eps, void *stream) {
+  if (!d_params || !d_grad || !d_m || !d_v) return set_err(FA_ERR_ARG, "null pointer");
+  if (step < 1) return set_err(FA_ERR_ARG, "step must be >= 1");
+  const float c1 = static_cast<float>(1.0 / (1.0 - std::pow(static_cast<double>(beta1), step)));
+  const float c2 = static_cast<float>(1.0 / (1.0 - std::pow(static_cast<double>(beta2), step)));
+  FA_CUDA(fa::launch_adam(d_params, d_grad, d_m, d_v, lr, beta1, beta2, eps, c1, c2,
+                          static_cast<cudaStream_t>(stream)));
+  return FA_OK;
+}
 
 fa_status fa_batch_plan(fa_batch_t *out, int count, const int *ns, const int *flows,
                         const double *Ts, const int *coarse_steps, int N, int fine_steps,

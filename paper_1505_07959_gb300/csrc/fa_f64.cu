@@ -46,6 +46,7 @@ __device__ __forceinline__ void epi_f64(const EpiParams &e, int b, int i, int j,
       break;
     }
     case EPI_PROD:
+    case EPI_TAYLOR:
       e.out64[b * nn + r] = v;
       break;
     case EPI_EULER: {
@@ -66,7 +67,8 @@ __device__ __forceinline__ void epi_f64(const EpiParams &e, int b, int i, int j,
       break;
     }
     default:
-      e.store_out[b * nn + r] = e.alpha * v + (i == j ? e.beta : 0.0);
+      e.store_out[b * nn + r] = e.alpha * v + (i == j ? e.beta : 0.0) +
+                                (e.store_add ? e.store_add[b * nn + r] : 0.0);
       break;
   }
 }

@@ -32,6 +32,7 @@ enum EpiMode : int {
   EPI_PROD = 1,    // write the product as operand terms (inverse flow: P = (I-A) Y)
   EPI_EULER = 2,   // forward-Euler substep of G, with the parareal correction on the last one
   EPI_STORE = 3,   // plain float64 store: out = alpha * v + beta * (i == j)
+  EPI_TAYLOR = 4,  // a product of a Taylor-term chain: float64 copy (out64) + operand terms
 };
 
 // Parameters of the fused epilogue.  One struct serves the tensor-core and the
@@ -72,9 +73,11 @@ struct EpiParams {
   const double *u_old;          // previous iterate U_{n+1} for the norms (0 = no norms)
   double *norm_part;            // per-tile partial sums [tiles][2]
   int euler_last;               // 1 on the last substep
-  // EPI_STORE
+  // EPI_STORE: store_out = alpha v + beta (i == j) (+ store_add when set), and the operand
+  // terms of that value (L and/or R form) when terms_l / terms_r are set
   double alpha, beta;
   double *store_out;
+  const double *store_add;
   int *err;                     // device error word
 };
 
@@ -175,6 +178,95 @@ cudaError_t launch_colmajor_pair(const double *A, int n, float *hi, float *lo, c
 cudaError_t launch_check_finite(const double *x, size_t count, int *err, cudaStream_t s);
 // X = I (row-major, count matrices)
 cudaError_t launch_identity(double *X, int n, cudaStream_t s);
+
+// --- learned coarse propagator (fa_learned.cu) ---
+// Slots of the per-block stats vector.
+enum StatSlot : int {
+  ST_HUT = 0,          // 8 Hutchinson sums z_k^T X z_k
+  ST_XX = 8,           // ||X||^2
+  ST_RR = 9,           // 10 Gram sums <R_a, R_b>, a <= b (rr_index)
+  ST_RD = 19,          // 4 sums <R_a, D>, D = F - X
+  ST_DD = 23,          // ||D||^2
+  ST_GLO = 24,         // Gershgorin lower bound (min over rows), when requested
+  ST_GHI = 25,         // Gershgorin upper bound (max over rows)
+  NSTAT = 26
+};
+
+// One stats pass over `nslices` slices (row-major float64 [slice][n][n] arrays).
+struct StatsArgs {
+  int n;
+  int rows_per_block;            // stats_rows_per_block(n)
+  const double *X;               // states
+  size_t x_stride;
+  const double *F;               // fine images (or D = F - G when G is set); null: no D sums
+  const double *G;               // added to F when not null
+  size_t f_stride;               // of F and G
+  const double *R[4];            // raw Taylor powers R_1..R_4 (nR = 0, 1 or 4 of them)
+  size_t r_stride;
+  int nR;
+  const uint8_t *probes;         // n bytes, bit k = sign of probe k
+  int gersh;                     // 1: Gershgorin bounds of X
+  double *part;                  // [nslices][stats_blocks(n)][NSTAT]
+};
+
+// Taylor scale s_a = dT^(a+1) kappa_a of the raw power R_(a+1).
+struct RecordScale {
+  double s[4];
+};
+
+// Per-sample activations and gradients kept between the two training kernels.
+struct MlpTrainBuffers {
+  double *loss;
+  float *xs, *h1, *h2, *dz1, *dz2, *dc;
+};
+
+// The learned coarse step's update on one slice (row-major float64 n x n).
+struct CombineArgs {
+  int n;
+  const double *v_in;            // X
+  const double *R[4];            // raw powers R_1..R_4
+  double scale[4];               // s_j = dT^j kappa_j
+  const float *coef;             // c_1..c_4 (device)
+  const double *d_in;            // correction D_n, or null (Step 0)
+  const double *u_old;           // previous iterate for the norms, or null
+  double *g_out;                 // G_theta(X)
+  double *v_out;                 // X_{n+1} = G + D
+  double *norm_part;             // [blocks][2], or null
+};
+
+int stats_rows_per_block(int n);
+int stats_blocks(int n);
+cudaError_t launch_probes(int n, uint8_t *bits, cudaStream_t s);
+cudaError_t launch_stats(const StatsArgs &a, int nslices, cudaStream_t s);
+// mstats[0..2] = Gershgorin lower / upper bound, Hutchinson tr(A), from a one-slice stats pass.
+cudaError_t launch_matrix_stats(const double *part, int n, double *mstats, cudaStream_t s);
+cudaError_t launch_records(const double *part, int nslices, int n, int N_total, int slice0,
+                           double dT, const RecordScale &sc, const double *mstats, double *rec,
+                           cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *P, int B, const double *feat, int fstride, float *coef,
+                               int *fallbacks, cudaStream_t s);
+size_t mlp_train_scratch_bytes(int B);
+cudaError_t launch_mlp_loss_grad(const float *P, int B, const double *rec, void *scratch,
+                                 float *grad, double *loss, cudaStream_t s);
+cudaError_t launch_adam(float *P, const float *grad, float *m, float *v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_coarse_coef(const float *P, const double *part, int n, int slice, int N,
+                               double dT, const double *mstats, float *coef, int *fallbacks,
+                               cudaStream_t s);
+cudaError_t launch_combine(const CombineArgs &a, int blocks, cudaStream_t s);
+
+// --- square-root refinement helpers (fa_refine.cu) ---
+constexpr int kDevNormBlocks = 256;
+// One power-iteration step: y = X v, lam = ||y||, v = y / ||y||.
+cudaError_t launch_power_step(const double *X, int n, double *v, double *y, double *lam,
+                              cudaStream_t s);
+// out = a (A + A^T)/2 + b B + c (C + C^T)/2 (null operands skipped; out may alias B).
+cudaError_t launch_sym_combine(int n, double a, const double *A, double b, const double *B,
+                               double c, const double *C, double *out, cudaStream_t s);
+cudaError_t launch_fill(double *x, size_t count, double v, cudaStream_t s);
+// *out = ||T - d I||_F^2 (part: kDevNormBlocks doubles of scratch), fixed order.
+cudaError_t launch_dev_norm(const double *T, int n, double d, double *part, double *out,
+                            cudaStream_t s);
 
 // Per-thread launch counter (incremented by every launcher).
 void count_launch();

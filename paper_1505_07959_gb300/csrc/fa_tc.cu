@@ -298,6 +298,66 @@ __device__ __forceinline__ void euler_chunk(const EpiParams &e, int i, int j0, i
   }
 }
 
+// Operand terms (L form and/or R form) of 32 float values of row i, columns j0.. of slice b.
+__device__ __forceinline__ void write_terms(const EpiParams &e, int b, int i, int j0, int cnt,
+                                            const float (&w)[32]) {
+  const int n = e.n;
+#pragma unroll
+  for (int h8 = 0; h8 < 4; ++h8) {
+    Terms3 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = split3_f32(w[8 * h8 + u]);
+    if (e.terms_r) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (8 * h8 + u < cnt) put_r(e, b, i, j0 + 8 * h8 + u, t[u]);
+    }
+    if (e.terms_l) {
+      const size_t off = (static_cast<size_t>(b) * n + i) * e.ldp + j0 + 8 * h8;
+      if (8 * h8 + 8 <= cnt) {
+        put_l8(e, off, t);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (8 * h8 + u < cnt) put_l1(e, off + u, t[u]);
+      }
+    }
+  }
+}
+
+// One product R of a Taylor-term chain (the learned coarse propagator's X_[j]): its float64
+// copy, row-major, in out64 (when set), and the operand terms of R that the chain's next product
+// reads (L form and/or R form, from the float32 value).
+__device__ __forceinline__ void taylor_chunk(const EpiParams &e, int b, int i, int j0, int cnt,
+                                             const float (&v)[32]) {
+  const int n = e.n;
+  if (e.out64) {
+    double *o = e.out64 + static_cast<size_t>(b) * n * n + static_cast<size_t>(i) * n + j0;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj)
+      if (jj < cnt) o[jj] = static_cast<double>(v[jj]);
+  }
+  if (e.terms_r || e.terms_l) write_terms(e, b, i, j0, cnt, v);
+}
+
+// Plain store: alpha v + beta (i == j) (+ the addend), float64 row-major, and its operand terms.
+__device__ __forceinline__ void store_chunk(const EpiParams &e, int b, int i, int j0, int cnt,
+                                            const float (&v)[32]) {
+  const int n = e.n;
+  const size_t r0 = static_cast<size_t>(b) * n * n + static_cast<size_t>(i) * n + j0;
+  float w[32];
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    double val = e.alpha * static_cast<double>(v[jj]) + (i == j0 + jj ? e.beta : 0.0);
+    if (jj < cnt) {
+      if (e.store_add) val += e.store_add[r0 + jj];
+      if (e.store_out) e.store_out[r0 + jj] = val;
+    }
+    w[jj] = static_cast<float>(val);
+  }
+  if (e.terms_r || e.terms_l) write_terms(e, b, i, j0, cnt, w);
+}
+
 // Where a tile of the launch lives: its problem's tensor maps and epilogue, and its position.
 struct TileInfo {
   const CUtensorMap *tmL, *tmR;
@@ -647,13 +707,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (jj < cnt) put_r(e, gb, i, j0 + jj, split3_f32(v[jj]));
         } else if (e.mode == EPI_EULER) {
           euler_chunk(e, i, j0, cnt, v, s0, s1);
+        } else if (e.mode == EPI_TAYLOR) {
+          taylor_chunk(e, gb, i, j0, cnt, v);
         } else {
-          const size_t r0 = gb * static_cast<size_t>(n) * n + static_cast<size_t>(i) * n + j0;
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            if (jj < cnt)
-              e.store_out[r0 + jj] =
-                  e.alpha * static_cast<double>(v[jj]) + (i == j0 + jj ? e.beta : 0.0);
+          store_chunk(e, gb, i, j0, cnt, v);
         }
       }
       ptx::tc_fence_before();

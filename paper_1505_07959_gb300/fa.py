@@ -27,7 +27,13 @@ SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_s
            "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
            "fa_debug_product", "fa_debug_set_profile", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
            "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
-           "fa_batch_solve", "fa_batch_destroy"]
+           "fa_batch_solve", "fa_batch_destroy", "fa_plan_set_learned", "fa_plan_learned_coefs",
+           "fa_learned_records_scratch", "fa_learned_records", "fa_plan_set_recorder",
+           "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam"]
+FA_COARSE_EULER, FA_COARSE_LEARNED = 0, 1
+FA_MLP_FEATURES, FA_MLP_HIDDEN, FA_MLP_COEFS, FA_MLP_PARAMS = 8, 128, 4, 18196
+FA_RECORD_DOUBLES = 32
+FA_PROBES, FA_PROBE_SEED = 8, 0x150507959
 
 
 class fa_problem_desc(ctypes.Structure):
@@ -35,14 +41,15 @@ class fa_problem_desc(ctypes.Structure):
                 ("N", ctypes.c_int), ("coarse_steps", ctypes.c_int), ("fine_steps", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
                 ("fine_dtype", ctypes.c_int), ("coarse_dtype", ctypes.c_int),
-                ("refine_steps", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("coarse_kind", ctypes.c_int)]
 
 
 class fa_report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("last_dx", ctypes.c_double),
                 ("t_init_ms", ctypes.c_double), ("t_fine_ms", ctypes.c_double),
                 ("t_coarse_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double),
-                ("dx_history", ctypes.POINTER(ctypes.c_double))]
+                ("dx_history", ctypes.POINTER(ctypes.c_double)), ("g_fallback_iter", ctypes.c_int),
+                ("coef_fallbacks", ctypes.c_int), ("records", ctypes.c_int)]
 
 
 class FaError(RuntimeError):
@@ -85,6 +92,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_batch_solve": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_double)],
         "fa_batch_destroy": [vp],
+        "fa_plan_set_learned": [vp, dp],
+        "fa_plan_learned_coefs": [vp, dp],
+        "fa_learned_records_scratch": [vp, ctypes.POINTER(sz)],
+        "fa_learned_records": [vp, dp, dp, dp, dp, sz],
+        "fa_plan_set_recorder": [vp, dp, ctypes.c_int, dp, sz],
+        "fa_mlp_forward": [dp, ctypes.c_int, dp, ctypes.c_int, dp, vp],
+        "fa_mlp_scratch_bytes": [ctypes.c_int, ctypes.POINTER(sz)],
+        "fa_mlp_loss_grad": [dp, ctypes.c_int, dp, dp, dp, dp, sz, vp],
+        "fa_mlp_adam": [dp, dp, dp, dp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                        ctypes.c_float, ctypes.c_float, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -221,13 +238,62 @@ def fa_batch_destroy(h):
         _LIB.fa_batch_destroy(h)
 
 
+def fa_plan_set_learned(h, d_params):
+    _check(load_library().fa_plan_set_learned(h, _ptr(d_params)))
+
+
+def fa_plan_learned_coefs(h, d_coef):
+    _check(load_library().fa_plan_learned_coefs(h, _ptr(d_coef)))
+
+
+def fa_learned_records_scratch(h) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().fa_learned_records_scratch(h, ctypes.byref(b)))
+    return b.value
+
+
+def fa_learned_records(h, dU, dF, d_records, d_scratch, scratch_bytes: int):
+    _check(load_library().fa_learned_records(h, _ptr(dU), _ptr(dF), _ptr(d_records),
+                                             _ptr(d_scratch), scratch_bytes))
+
+
+def fa_plan_set_recorder(h, d_records, capacity: int, d_scratch, scratch_bytes: int):
+    _check(load_library().fa_plan_set_recorder(h, _ptr(d_records), int(capacity), _ptr(d_scratch),
+                                               scratch_bytes))
+
+
+def fa_mlp_forward(d_params, batch: int, d_feat, feat_stride: int, d_coef, stream_handle: int):
+    _check(load_library().fa_mlp_forward(_ptr(d_params), batch, _ptr(d_feat), feat_stride,
+                                         _ptr(d_coef), ctypes.c_void_p(stream_handle)))
+
+
+def fa_mlp_scratch_bytes(batch: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().fa_mlp_scratch_bytes(batch, ctypes.byref(b)))
+    return b.value
+
+
+def fa_mlp_loss_grad(d_params, batch: int, d_records, d_grad, d_loss, d_scratch,
+                     scratch_bytes: int, stream_handle: int):
+    _check(load_library().fa_mlp_loss_grad(_ptr(d_params), batch, _ptr(d_records), _ptr(d_grad),
+                                           _ptr(d_loss), _ptr(d_scratch), scratch_bytes,
+                                           ctypes.c_void_p(stream_handle)))
+
+
+def fa_mlp_adam(d_params, d_grad, d_m, d_v, step: int, lr: float, beta1: float, beta2: float,
+                eps: float, stream_handle: int):
+    _check(load_library().fa_mlp_adam(_ptr(d_params), _ptr(d_grad), _ptr(d_m), _ptr(d_v), step,
+                                      lr, beta1, beta2, eps, ctypes.c_void_p(stream_handle)))
+
+
 # --- convenience wrapper ----------------------------------------------------------------------
 
 class Plan:
     """A plan plus its PyTorch-allocated workspace, on the current CUDA stream."""
 
     def __init__(self, n, flow, T, N, fine_steps, coarse_steps=1, max_iters=None, tol=0.0,
-                 fine_dtype="f64", coarse_dtype=None, refine_steps=0, stream=None):
+                 fine_dtype="f64", coarse_dtype=None, refine_steps=0, stream=None,
+                 coarse_kind=FA_COARSE_EULER):
         import torch
 
         self.torch = torch
@@ -238,7 +304,7 @@ class Plan:
                                     fine_steps=fine_steps,
                                     max_iters=N if max_iters is None else max_iters,
                                     tol=float(tol), fine_dtype=fd, coarse_dtype=cd,
-                                    refine_steps=refine_steps)
+                                    refine_steps=refine_steps, coarse_kind=int(coarse_kind))
         self.n, self.N = n, N
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle, self.ws_bytes = fa_plan(self.desc, self.stream.cuda_stream)
@@ -310,6 +376,44 @@ class Plan:
         st = fa_parareal_solve_host(self.handle, A, X0, X, rep)
         return X, _report(rep, hist, st)
 
+    def set_learned(self, params):
+        """Install the coefficient network (float32 blob of FA_MLP_PARAMS values)."""
+        self.params = self.torch.as_tensor(params, dtype=self.torch.float32).cuda().contiguous()
+        assert self.params.numel() == FA_MLP_PARAMS
+        fa_plan_set_learned(self.handle, self.params)
+
+    def learned_coefs(self):
+        c = self.torch.empty((self.N, FA_MLP_COEFS), dtype=self.torch.float32, device="cuda")
+        fa_plan_learned_coefs(self.handle, c)
+        return c
+
+    def _records_scratch(self):
+        if getattr(self, "rec_scratch", None) is None:
+            nb = fa_learned_records_scratch(self.handle)
+            self.rec_scratch = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+        return self.rec_scratch
+
+    def records(self, U, F):
+        """Pair records (N, FA_RECORD_DOUBLES) of the states U[b] and their fine images F[b]."""
+        U = self._f64(U, (self.N, self.n, self.n))
+        F = self._f64(F, (self.N, self.n, self.n))
+        out = self.torch.empty((self.N, FA_RECORD_DOUBLES), dtype=self.torch.float64, device="cuda")
+        sc = self._records_scratch()
+        fa_learned_records(self.handle, U, F, out, sc, sc.numel())
+        return out
+
+    def set_recorder(self, capacity):
+        """Record up to `capacity` training pairs during the next solves (None: off)."""
+        if capacity is None:
+            fa_plan_set_recorder(self.handle, None, 0, None, 0)
+            self.rec_buf = None
+            return None
+        self.rec_buf = self.torch.zeros((capacity, FA_RECORD_DOUBLES), dtype=self.torch.float64,
+                                        device="cuda")
+        sc = self._records_scratch()
+        fa_plan_set_recorder(self.handle, self.rec_buf, capacity, sc, sc.numel())
+        return self.rec_buf
+
     def close(self):
         if getattr(self, "handle", None):
             fa_plan_destroy(self.handle)
@@ -320,6 +424,49 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """The coefficient network's kernels on one parameter blob (training state on the device)."""
+
+    def __init__(self, params, stream=None):
+        import torch
+
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = torch.as_tensor(params, dtype=torch.float32).cuda().contiguous().clone()
+        assert self.params.numel() == FA_MLP_PARAMS
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.step = 0
+        self.scratch = None
+
+    def forward(self, feat, stride=None):
+        """feat: (B, >= 8) float64 CUDA tensor (e.g. records) -> (B, 4) float32 coefficients."""
+        feat = feat.contiguous()
+        B = feat.shape[0]
+        out = self.torch.empty((B, FA_MLP_COEFS), dtype=self.torch.float32, device="cuda")
+        fa_mlp_forward(self.params, B, feat, feat.shape[1] if stride is None else stride, out,
+                       self.stream.cuda_stream)
+        return out
+
+    def loss_grad(self, records):
+        """Mean loss and gradient of a batch of records (float64 CUDA (B, FA_RECORD_DOUBLES))."""
+        records = records.contiguous()
+        B = records.shape[0]
+        need = fa_mlp_scratch_bytes(B)
+        if self.scratch is None or self.scratch.numel() < need:
+            self.scratch = self.torch.empty(need, dtype=self.torch.uint8, device="cuda")
+        fa_mlp_loss_grad(self.params, B, records, self.grad, self.loss, self.scratch,
+                         self.scratch.numel(), self.stream.cuda_stream)
+        return self.loss, self.grad
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        fa_mlp_adam(self.params, self.grad, self.m, self.v, self.step, lr, beta1, beta2, eps,
+                    self.stream.cuda_stream)
 
 
 class Batch:
@@ -365,4 +512,6 @@ def _report(rep: fa_report, hist, status) -> dict:
     return {"iters": rep.iters, "converged": bool(rep.converged), "last_dx": rep.last_dx,
             "dx_history": [hist[i] for i in range(rep.iters)], "t_init_ms": rep.t_init_ms,
             "t_fine_ms": rep.t_fine_ms, "t_coarse_ms": rep.t_coarse_ms,
-            "t_refine_ms": rep.t_refine_ms, "status": status}
+            "t_refine_ms": rep.t_refine_ms, "status": status,
+            "g_fallback_iter": rep.g_fallback_iter, "coef_fallbacks": rep.coef_fallbacks,
+            "records": rep.records}
