@@ -276,6 +276,7 @@ TcGemmParams tc_launch_params(int n, int nb, int l_batched, int r_batched, const
   g.kblocks = (n + 63) / 64;
   tc_schedule(ps, g);
   g.prof = g_prof;
+  g.prefetch_state = ps.npairs == 1 ? 1 : 0;   // measured: +10 % at one pair, -2 % at six
   g.idesc = ptx::idesc_bf16_f32(TC_BM, TC_BN);
   return g;
 }

@@ -109,6 +109,9 @@ struct TcGemmParams {
   int pair_tl[kMaxPairs], pair_tr[kMaxPairs], pair_at[kMaxPairs];
   uint32_t idesc;   // tcgen05 instruction descriptor
   unsigned long long *prof;   // optional per-role cycle counters (diagnostics), may be null
+  int prefetch_state;         // 1: the epilogue warps prefetch their tile's state into L2 while
+                              // the tile's products run (pays where the epilogue dominates:
+                              // one term pair; with six it competes with the operand feed)
   const TcSegment *segs;      // ragged launch: per-problem segments (device), else null
   int nseg;
   EpiParams epi;

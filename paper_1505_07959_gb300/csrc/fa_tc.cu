@@ -358,6 +358,52 @@ __device__ __forceinline__ void store_chunk(const EpiParams &e, int b, int i, in
   if (e.terms_r || e.terms_l) write_terms(e, b, i, j0, cnt, w);
 }
 
+// Prefetch into L2 the state that the epilogue of tile (mt, ntile) of slice b will read, for the
+// 32 rows of this warp's TMEM lane quarter: issued while the store warps wait for the tile's
+// products, it turns the epilogue's dependent HBM loads into L2 hits.  Column-major state (RK4
+// stage arrays, A's float32 pair): one 32-row segment (<= two lines) per column, lane + 32 k
+// columns per lane; row-major state (Euler / store addends): the row's 128 columns.
+__device__ __forceinline__ void prefetch_tile_state(const EpiParams &e, int b, int mt, int ntile,
+                                                    int q, int lane) {
+  const int n = e.n;
+  const int i0 = mt * BM + q * 32;
+  if (i0 >= n) return;
+  const size_t nn = static_cast<size_t>(n) * n;
+  if (e.mode == EPI_STAGE) {
+    const int last = n - 1 - i0 < 31 ? n - 1 - i0 : 31;     // last row of the segment inside n
+    const float *arr[5] = {e.x_hi, e.stage > 1 ? e.acc : nullptr, e.stage == 4 ? e.x_lo : nullptr,
+                           e.flow == FA_FLOW_SQRT ? e.a_hi : nullptr,
+                           e.flow == FA_FLOW_SQRT ? e.a_lo : nullptr};
+#pragma unroll
+    for (int k = 0; k < BN / 32; ++k) {
+      const int j = ntile * BN + lane + 32 * k;
+      if (j >= n) break;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        if (!arr[a]) continue;
+        const float *c = arr[a] + (a < 3 ? b * nn : 0) + static_cast<size_t>(j) * n + i0;
+        ptx::prefetch_l2(c);
+        ptx::prefetch_l2(c + last);
+      }
+    }
+  } else if (e.mode == EPI_EULER || (e.mode == EPI_STORE && e.store_add)) {
+    const int i = i0 + lane;
+    if (i >= n) return;
+    const double *arr[3] = {e.mode == EPI_EULER ? e.v_in : e.store_add,
+                            e.mode == EPI_EULER ? e.d_in : nullptr,
+                            e.mode == EPI_EULER ? e.u_old : nullptr};
+    const int j0 = ntile * BN;
+    const int cnt = n - j0 < BN ? n - j0 : BN;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!arr[a]) continue;
+      const double *r = arr[a] + (e.mode == EPI_STORE ? b * nn : 0) + static_cast<size_t>(i) * n + j0;
+      for (int c = 0; c < cnt; c += 16) ptx::prefetch_l2(r + c);
+      ptx::prefetch_l2(r + cnt - 1);
+    }
+  }
+}
+
 // Where a tile of the launch lives: its problem's tensor maps and epilogue, and its position.
 struct TileInfo {
   const CUtensorMap *tmL, *tmR;
@@ -670,6 +716,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
       const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lslice, gb = ti_.gb;
       const int i = mt * BM + row;
+      if (p.prefetch_state) prefetch_tile_state(e, gb, mt, ntile, q, lane);
       if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
         fail(abort_flag, err);
         break;
