@@ -246,6 +246,29 @@ fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *d
                          double *last_dx);
 fa_status fa_batch_destroy(fa_batch_t b);
 
+/* Autotune a batch's launch schedule (not part of the paper's method).  Knobs: per size bucket
+ * of n (<= 64, 128, 256, 512, 1024, larger), whether the epilogue prefetches its tile's state
+ * into L2 while the tile's products run, and the tile order inside a slice (M-tile or N-tile
+ * fastest); per launch, the order of the problems in the ragged tile list (as given, or largest
+ * n first).  Coordinate descent from the defaults, timing the batch's own fine-sweep stage
+ * launch (CUDA events, 3 repetitions) on the matrices dA; a change is kept when it saves more
+ * than 1 %.  None of the knobs changes any result bit (each tile's arithmetic and the order of
+ * every reduction are fixed).  If `cache_path` names a file holding an entry for this batch
+ * (its count, N, J, dtype and a signature of the problems' n, flow, T and m), that schedule is
+ * used without timing; otherwise the tuned schedule is appended to the file.  NULL: no file.
+ * Synchronises the batch's stream.  Call after fa_batch_bind_workspace (which resets the
+ * schedule to the defaults). */
+fa_status fa_batch_autotune(fa_batch_t b, const double *const *dA, const char *cache_path);
+/* One-line account of the last fa_batch_autotune (choices and timings); "" before one. */
+const char *fa_batch_tuning(fa_batch_t b);
+
+/* The same for one plan: times its fine-sweep stage product(s) with each combination of the
+ * epilogue prefetch and the tile order (the plan's matrix must be set) and keeps the fastest
+ * (more than 1 % better than the first) for all its tensor-core launches.  No-op for float64
+ * plans.  Results do not change.  fa_plan_tuning returns the account. */
+fa_status fa_plan_autotune(fa_plan_t p);
+const char *fa_plan_tuning(fa_plan_t p);
+
 /* ---- Learned coarse propagator ----------------------------------------------------------
  *
  * Not part of the paper's method: a coarse propagator whose coefficients are learned from

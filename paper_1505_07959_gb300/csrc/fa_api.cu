@@ -1,5 +1,6 @@
 // Host driver and C ABI of libfa: plans, workspace layout, the fine and
 // coarse sweeps of classical parareal (Algorithm 1) and the solve loop.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -144,6 +145,9 @@ struct fa_plan_s {
   CUtensorMap tmLp[2]{}, tmLt{}, tmLq{}, tmLpq{};
   size_t strideS = 0;
   int sign_steps_last = 0;       // sign-iteration steps of the last Newton step (diagnostics)
+  // launch schedule of the tensor-core products (fa_plan_autotune; -1 = the default rule)
+  int tune_prefetch = -1, tune_raster = -1;
+  std::string tuning;
   // pair recorder of fa_parareal_solve
   double *rec = nullptr;
   int rec_cap = 0, rec_count = 0;
@@ -348,6 +352,8 @@ EpiParams base_epi(const fa_plan_s *p) {
 TcGemmParams tc_params(const fa_plan_s *p, int nb, int l_batched, int r_batched,
                        const EpiParams &e) {
   TcGemmParams g = fa::tc_launch_params(p->d.n, nb, l_batched, r_batched, p->ps);
+  if (p->tune_prefetch >= 0) g.prefetch_state = p->tune_prefetch;
+  if (p->tune_raster >= 0) g.raster = p->tune_raster;
   g.epi = e;
   return g;
 }
@@ -957,6 +963,12 @@ struct fa_batch_s {
   std::vector<Table> coarse;     // [((mode * N + n) * max_m + sub) * 2 + phase]
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
+  // launch schedule of the fine-sweep tables (fa_batch_autotune): per size bucket of n, the
+  // epilogue's L2 prefetch and the tile order; per launch, the order of the problems
+  static constexpr int kBuckets = 6;     // n <= 64, 128, 256, 512, 1024, larger
+  int prefetch_b[kBuckets] = {0, 0, 0, 0, 0, 0}, raster_b[kBuckets] = {0, 0, 0, 0, 0, 0};
+  int order = 0;                         // 0: problems as given, 1: largest n first
+  std::string tuning;
   ~fa_batch_s() {
     for (auto *p : plans) delete p;
     if (graph) cudaGraphExecDestroy(graph);
@@ -968,9 +980,25 @@ struct fa_batch_s {
 
 namespace {
 
+int size_bucket(int n) {
+  int k = 0;
+  for (int edge = 64; k < fa_batch_s::kBuckets - 1 && n > edge; edge *= 2) ++k;
+  return k;
+}
+
+// Problem indices in the order of the batch's segment tables.
+std::vector<int> problem_order(const fa_batch_s *b) {
+  std::vector<int> ord(b->count);
+  for (int i = 0; i < b->count; ++i) ord[i] = i;
+  if (b->order == 1)
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int x, int y) { return b->plans[x]->d.n > b->plans[y]->d.n; });
+  return ord;
+}
+
 void push_segment(std::vector<fa::TcSegment> &host, fa_batch_s::Table &t, const fa_plan_s *p,
                   const CUtensorMap &L, const CUtensorMap &R, int nb, int lbat, int rbat,
-                  const EpiParams &e) {
+                  const EpiParams &e, int prefetch = -1, int raster = 0) {
   fa::TcSegment sg;
   memset(&sg, 0, sizeof(sg));
   sg.tmL = L;
@@ -983,6 +1011,8 @@ void push_segment(std::vector<fa::TcSegment> &host, fa_batch_s::Table &t, const 
   sg.mt = (p->d.n + TC_BM - 1) / TC_BM;
   sg.nt = (p->d.n + TC_BN - 1) / TC_BN;
   sg.kblocks = (p->d.n + 63) / 64;
+  sg.prefetch = prefetch >= 0 ? prefetch : (p->ps.npairs == 1 ? 1 : 0);
+  sg.raster = raster;
   sg.tile_begin = t.tiles;
   t.tiles += sg.mt * sg.nt * nb;
   ++t.nseg;
@@ -994,6 +1024,7 @@ void push_segment(std::vector<fa::TcSegment> &host, fa_batch_s::Table &t, const 
 void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
   host.clear();
   const int N = b->N, J = b->J;
+  const std::vector<int> ord = problem_order(b);
   // fine sweep: config c = stage 1..4 (c = 0..3), or stage 4 of the last step (c = 4)
   for (int c = 0; c < 5; ++c) {
     const int st = c < 4 ? c + 1 : 4;
@@ -1003,8 +1034,11 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
       fa_batch_s::Table &t = b->fine[c][phase];
       t = fa_batch_s::Table();
       t.first = host.size();
-      for (fa_plan_s *p : b->plans) {
+      for (int idx : ord) {
+        fa_plan_s *p = b->plans[idx];
         const fa_problem_desc &d = p->d;
+        const int bk = size_bucket(d.n);
+        const int pf = b->prefetch_b[bk], rs = b->raster_b[bk];
         const double h = d.T / static_cast<double>(N) / static_cast<double>(J);
         EpiParams e = base_epi(p);
         e.mode = fa::EPI_STAGE;
@@ -1027,9 +1061,9 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
         e.err = b->d_err;
         if (phase == 0) {
           if (d.flow == FA_FLOW_EXP) {
-            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e);
+            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e, pf, rs);
           } else if (d.flow == FA_FLOW_SQRT) {
-            push_segment(host, t, p, p->tmYl[cur], p->tmYr[cur], N, 1, 1, e);
+            push_segment(host, t, p, p->tmYl[cur], p->tmYr[cur], N, 1, 1, e, pf, rs);
           } else {
             EpiParams e1 = base_epi(p);
             e1.mode = fa::EPI_PROD;
@@ -1037,10 +1071,10 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
             e1.terms_r = p->ps.terms_r;
             e1.term_stride_r = p->strideY;
             e1.err = b->d_err;
-            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e1);
+            push_segment(host, t, p, p->tmA, p->tmYr[cur], N, 0, 1, e1, pf, rs);
           }
         } else if (d.flow == FA_FLOW_INV) {
-          push_segment(host, t, p, p->tmYl[cur], p->tmPr, N, 1, 1, e);
+          push_segment(host, t, p, p->tmYl[cur], p->tmPr, N, 1, 1, e, pf, rs);
         }
       }
     }
@@ -1053,7 +1087,8 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
         for (int phase = 0; phase < 2; ++phase) {
           fa_batch_s::Table &t = b->coarse[b->coarse_index(mode, n, sub, phase)];
           t.first = host.size();
-          for (fa_plan_s *p : b->plans) {
+          for (int idx : ord) {
+            fa_plan_s *p = b->plans[idx];
             const fa_problem_desc &d = p->d;
             const int m = d.coarse_steps;
             if (sub >= m) continue;
@@ -1100,6 +1135,24 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
               push_segment(host, t, p, p->tmVl[cur], p->tmPcr, 1, 0, 0, e);
           }
         }
+}
+
+// Segment tables to the device (after any change of the schedule); the captured iteration
+// graph refers to the old tables' contents only through the device array, but is rebuilt anyway.
+fa_status upload_tables(fa_batch_s *b) {
+  std::vector<fa::TcSegment> host;
+  host.reserve(b->nseg_total);
+  build_tables(b, host);
+  if (host.size() > b->nseg_total) return set_err(FA_ERR_WORKSPACE, "segment table overflow");
+  FA_CUDA(cudaMemcpyAsync(b->d_segs, host.data(), host.size() * sizeof(fa::TcSegment),
+                          cudaMemcpyHostToDevice, b->stream));
+  FA_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->graph_tried = false;
+  return FA_OK;
 }
 
 fa_status launch_table(fa_batch_s *b, const fa_batch_s::Table &t) {
@@ -1606,12 +1659,13 @@ fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_ws, size_t bytes) {
     fa_plan_s *p = b->plans[i];
     FA_TRY(fa_plan_bind_workspace(p, b->ws + b->offs[i], p->ws_need));
   }
-  std::vector<fa::TcSegment> host;
-  host.reserve(b->nseg_total);
-  build_tables(b, host);
-  if (host.size() > b->nseg_total) return set_err(FA_ERR_WORKSPACE, "segment table overflow");
-  FA_CUDA(cudaMemcpyAsync(b->d_segs, host.data(), host.size() * sizeof(fa::TcSegment),
-                          cudaMemcpyHostToDevice, b->stream));
+  const int pf = b->plans[0]->ps.npairs == 1 ? 1 : 0;
+  for (int k = 0; k < fa_batch_s::kBuckets; ++k) {
+    b->prefetch_b[k] = pf;
+    b->raster_b[k] = 0;
+  }
+  b->order = 0;
+  FA_TRY(upload_tables(b));
   std::vector<fa::BatchNorm> norms(b->count);
   for (int i = 0; i < b->count; ++i) {
     norms[i].part = b->plans[i]->part;
@@ -1620,13 +1674,249 @@ fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_ws, size_t bytes) {
   FA_CUDA(cudaMemcpyAsync(b->d_norm, norms.data(), norms.size() * sizeof(fa::BatchNorm),
                           cudaMemcpyHostToDevice, b->stream));
   FA_CUDA(cudaStreamSynchronize(b->stream));
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
-  b->graph_tried = false;
   return FA_OK;
 }
+
+namespace {
+
+// Valid operands for timing launches: every slice of U = I, the RK4 state loaded from it.
+fa_status timing_state(fa_plan_s *p, cudaStream_t s) {
+  for (int k = 0; k < p->d.N; ++k)
+    FA_CUDA(fa::launch_identity(p->U + static_cast<size_t>(k) * p->nn, p->d.n, s));
+  if (p->mixed)
+    FA_CUDA(fa::launch_load_state(p->U, p->d.N, p->d.n, p->ldp, p->x_hi, p->x_lo, p->Yl[0],
+                                  p->needs_l() ? p->ps.terms_l : 0, p->strideY, p->Yr[0],
+                                  p->ps.terms_r, p->strideY, s));
+  return FA_OK;
+}
+
+// A short signature of a batch's problems (FNV-1a over n, flow, T and m).
+unsigned long long batch_signature(const fa_batch_s *b) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    for (int k = 0; k < 8; ++k) {
+      h ^= (v >> (8 * k)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  for (const fa_plan_s *p : b->plans) {
+    unsigned long long tb;
+    memcpy(&tb, &p->d.T, sizeof(tb));
+    mix(static_cast<unsigned long long>(p->d.n));
+    mix(static_cast<unsigned long long>(p->d.flow));
+    mix(tb);
+    mix(static_cast<unsigned long long>(p->d.coarse_steps));
+  }
+  return h;
+}
+
+std::string schedule_string(const fa_batch_s *b) {
+  std::string s = "order=" + std::to_string(b->order) + " buckets=";
+  for (int k = 0; k < fa_batch_s::kBuckets; ++k) {
+    if (k) s += ",";
+    s += std::to_string(b->prefetch_b[k]) + std::to_string(b->raster_b[k]);
+  }
+  return s;
+}
+
+bool parse_schedule(fa_batch_s *b, const char *line) {
+  int order = 0;
+  char bk[128] = {0};
+  if (sscanf(line, "order=%d buckets=%127s", &order, bk) != 2) return false;
+  int pf[fa_batch_s::kBuckets], rs[fa_batch_s::kBuckets];
+  const char *c = bk;
+  for (int k = 0; k < fa_batch_s::kBuckets; ++k) {
+    if (c[0] < '0' || c[0] > '1' || c[1] < '0' || c[1] > '1') return false;
+    pf[k] = c[0] - '0';
+    rs[k] = c[1] - '0';
+    c += 2;
+    if (k + 1 < fa_batch_s::kBuckets) {
+      if (*c != ',') return false;
+      ++c;
+    }
+  }
+  b->order = order ? 1 : 0;
+  for (int k = 0; k < fa_batch_s::kBuckets; ++k) {
+    b->prefetch_b[k] = pf[k];
+    b->raster_b[k] = rs[k];
+  }
+  return true;
+}
+
+}  // namespace
+
+fa_status fa_batch_autotune(fa_batch_t b, const double *const *dA, const char *cache_path) {
+  if (!b) return set_err(FA_ERR_ARG, "null batch");
+  if (!b->ws) return set_err(FA_ERR_WORKSPACE, "no workspace bound");
+  if (!dA) return set_err(FA_ERR_ARG, "null pointer");
+  char key[160];
+  snprintf(key, sizeof(key), "fa-batch count=%d N=%d J=%d dtype=%d sig=%016llx", b->count, b->N,
+           b->J, b->dtype, batch_signature(b));
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "r")) {
+      char line[512];
+      bool hit = false;
+      while (fgets(line, sizeof(line), f)) {
+        const size_t kl = strlen(key);
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ' && parse_schedule(b, line + kl + 1)) hit = true;
+      }
+      fclose(f);
+      if (hit) {
+        FA_TRY(upload_tables(b));
+        b->tuning = std::string("from cache: ") + schedule_string(b);
+        return FA_OK;
+      }
+    }
+  }
+  for (int i = 0; i < b->count; ++i) {
+    fa_plan_s *p = b->plans[i];
+    if (!dA[i]) return set_err(FA_ERR_ARG, "null pointer for problem %d", i);
+    p->err = b->d_err;
+    FA_TRY(fa_plan_set_matrix(p, dA[i]));
+    FA_TRY(timing_state(p, b->stream));
+  }
+  cudaEvent_t e0, e1;
+  FA_CUDA(cudaEventCreate(&e0));
+  FA_CUDA(cudaEventCreate(&e1));
+  // time of the fine sweep's stage-2 launches (both product phases), 3 repetitions
+  auto measure = [&](float *ms) -> fa_status {
+    FA_TRY(upload_tables(b));
+    FA_TRY(launch_table(b, b->fine[1][0]));
+    FA_TRY(launch_table(b, b->fine[1][1]));
+    FA_CUDA(cudaEventRecord(e0, b->stream));
+    for (int r = 0; r < 3; ++r) {
+      FA_TRY(launch_table(b, b->fine[1][0]));
+      FA_TRY(launch_table(b, b->fine[1][1]));
+    }
+    FA_CUDA(cudaEventRecord(e1, b->stream));
+    FA_CUDA(cudaEventSynchronize(e1));
+    FA_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.0f;
+    return FA_OK;
+  };
+  bool present[fa_batch_s::kBuckets] = {false, false, false, false, false, false};
+  for (const fa_plan_s *p : b->plans) present[size_bucket(p->d.n)] = true;
+  float best = 0.f, t = 0.f, base = 0.f;
+  fa_status st = measure(&best);
+  base = best;
+  std::string log;
+  // coordinate descent: keep a change only if it saves more than 1 %
+  auto trial = [&](int *knob, const char *name) -> fa_status {
+    *knob ^= 1;
+    const fa_status s2 = measure(&t);
+    if (s2 != FA_OK) return s2;
+    const bool keep = t < 0.99f * best;
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%s:%.3f%s ", name, t, keep ? "*" : "");
+    log += buf;
+    if (keep) best = t;
+    else *knob ^= 1;
+    return FA_OK;
+  };
+  if (st == FA_OK) st = trial(&b->order, "order");
+  for (int k = 0; st == FA_OK && k < fa_batch_s::kBuckets; ++k) {
+    if (!present[k]) continue;
+    char nm[32];
+    snprintf(nm, sizeof(nm), "b%d.prefetch", k);
+    st = trial(&b->prefetch_b[k], nm);
+    if (st != FA_OK) break;
+    snprintf(nm, sizeof(nm), "b%d.raster", k);
+    st = trial(&b->raster_b[k], nm);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FA_OK) return st;
+  FA_TRY(upload_tables(b));
+  char head[160];
+  snprintf(head, sizeof(head), "tuned: stage launch %.3f -> %.3f ms; ", base, best);
+  b->tuning = std::string(head) + schedule_string(b) + "; trials " + log;
+  if (cache_path) {
+    if (FILE *f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %s\n", key, schedule_string(b).c_str());
+      fclose(f);
+    } else {
+      return set_err(FA_ERR_ARG, "cannot write the tuning cache %s", cache_path);
+    }
+  }
+  return FA_OK;
+}
+
+const char *fa_batch_tuning(fa_batch_t b) { return b ? b->tuning.c_str() : ""; }
+
+fa_status fa_plan_autotune(fa_plan_t p) {
+  FA_TRY(check_ready(p, true));
+  if (!p->mixed) {
+    p->tuning = "float64 products: nothing to tune";
+    return FA_OK;
+  }
+  FA_TRY(timing_state(p, p->stream));
+  cudaEvent_t e0, e1;
+  FA_CUDA(cudaEventCreate(&e0));
+  FA_CUDA(cudaEventCreate(&e1));
+  const int N = p->d.N, tl = p->ps.terms_l, tr = p->ps.terms_r;
+  // the fine sweep's stage-2 product(s) under a schedule
+  auto stage = [&]() -> fa_status {
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_STAGE;
+    e.stage = 2;
+    e.h = 1e-3;
+    e.ch = 5e-4;
+    e.x_hi = p->x_hi;
+    e.x_lo = p->x_lo;
+    e.acc = p->acc;
+    e.a_hi = p->a_hi;
+    e.a_lo = p->a_lo;
+    e.out_r = p->Yr[1];
+    e.out_l = p->Yl[1];
+    e.terms_r = tr;
+    e.terms_l = p->needs_l() ? tl : 0;
+    e.term_stride_r = e.term_stride_l = p->strideY;
+    if (p->d.flow == FA_FLOW_EXP) return tc(p, p->tmA, p->tmYr[0], tc_params(p, N, 0, 1, e));
+    if (p->d.flow == FA_FLOW_SQRT) return tc(p, p->tmYl[0], p->tmYr[0], tc_params(p, N, 1, 1, e));
+    EpiParams e1 = base_epi(p);
+    e1.mode = fa::EPI_PROD;
+    e1.out_r = p->Pr;
+    e1.terms_r = tr;
+    e1.term_stride_r = p->strideY;
+    FA_TRY(tc(p, p->tmA, p->tmYr[0], tc_params(p, N, 0, 1, e1)));
+    return tc(p, p->tmYl[0], p->tmPr, tc_params(p, N, 1, 1, e));
+  };
+  float best = 1e30f;
+  int bp = 0, br = 0;
+  std::string log;
+  fa_status st = FA_OK;
+  for (int pf = 0; pf < 2 && st == FA_OK; ++pf)
+    for (int rs = 0; rs < 2 && st == FA_OK; ++rs) {
+      p->tune_prefetch = pf;
+      p->tune_raster = rs;
+      st = stage();
+      if (st != FA_OK) break;
+      cudaEventRecord(e0, p->stream);
+      for (int r = 0; r < 3 && st == FA_OK; ++r) st = stage();
+      cudaEventRecord(e1, p->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= 3.0f;
+      char buf[64];
+      snprintf(buf, sizeof(buf), "p%d r%d %.3f ms; ", pf, rs, ms);
+      log += buf;
+      if (ms < best * 0.99f) {
+        best = ms;
+        bp = pf;
+        br = rs;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FA_OK) return st;
+  p->tune_prefetch = bp;
+  p->tune_raster = br;
+  p->tuning = "chose prefetch=" + std::to_string(bp) + " raster=" + std::to_string(br) + " (" + log + ")";
+  return FA_OK;
+}
+
+const char *fa_plan_tuning(fa_plan_t p) { return p ? p->tuning.c_str() : ""; }
 
 fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *dXout, int *iters,
                          double *last_dx) {

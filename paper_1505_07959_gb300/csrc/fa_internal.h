@@ -87,6 +87,8 @@ struct alignas(64) TcSegment {
   CUtensorMap tmL, tmR;
   EpiParams epi;
   int n, nb, l_batched, r_batched, mt, nt, kblocks, tile_begin;
+  int prefetch;   // epilogue state prefetch into L2 for this problem's tiles (0 / 1)
+  int raster;     // tile order inside a slice: 0 = M-tile fastest, 1 = N-tile fastest
 };
 
 // One tensor-core GEMM launch: for every slice b in [0, nb) and tile,
@@ -109,6 +111,7 @@ struct TcGemmParams {
   int pair_tl[kMaxPairs], pair_tr[kMaxPairs], pair_at[kMaxPairs];
   uint32_t idesc;   // tcgen05 instruction descriptor
   unsigned long long *prof;   // optional per-role cycle counters (diagnostics), may be null
+  int raster;                 // uniform launches: 0 = M-tile fastest, 1 = N-tile fastest
   int prefetch_state;         // 1: the epilogue warps prefetch their tile's state into L2 while
                               // the tile's products run (pays where the epilogue dominates:
                               // one term pair; with six it competes with the operand feed)

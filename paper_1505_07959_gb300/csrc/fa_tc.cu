@@ -408,13 +408,14 @@ __device__ __forceinline__ void prefetch_tile_state(const EpiParams &e, int b, i
 struct TileInfo {
   const CUtensorMap *tmL, *tmR;
   const EpiParams *epi;
-  int mt, ntile, lslice, gb, lcoord, rcoord, kblocks, tiles_per_slice, tile_in_slice;
+  int mt, ntile, lslice, gb, lcoord, rcoord, kblocks, tiles_per_slice, tile_in_slice, prefetch;
 };
 
 __device__ __forceinline__ TileInfo tile_info(const TcGemmParams &p, const CUtensorMap *tmL,
                                               const CUtensorMap *tmR, int tile) {
   TileInfo t;
   int local = tile, mtc = p.mt, ntc = p.nt, lbat = p.l_batched, rbat = p.r_batched;
+  int raster = p.raster;
   if (p.segs) {
     int lo = 0, hi = p.nseg - 1;
     while (lo < hi) {
@@ -432,18 +433,28 @@ __device__ __forceinline__ TileInfo tile_info(const TcGemmParams &p, const CUten
     t.tmR = &sg->tmR;
     t.epi = &sg->epi;
     t.kblocks = sg->kblocks;
+    t.prefetch = sg->prefetch;
+    raster = sg->raster;
   } else {
     t.tmL = tmL;
     t.tmR = tmR;
     t.epi = &p.epi;
     t.kblocks = p.kblocks;
+    t.prefetch = p.prefetch_state;
   }
   t.tiles_per_slice = mtc * ntc;
-  t.tile_in_slice = local % t.tiles_per_slice;
-  t.mt = local % mtc;
-  const int rest = local / mtc;
-  t.ntile = rest % ntc;
-  t.lslice = rest / ntc;
+  const int pos = local % t.tiles_per_slice;    // position in the slice's traversal order
+  t.lslice = local / t.tiles_per_slice;
+  if (raster) {
+    t.ntile = pos % ntc;
+    t.mt = pos / ntc;
+  } else {
+    t.mt = pos % mtc;
+    t.ntile = pos / mtc;
+  }
+  // the tile's norm-partial slot does not depend on the traversal order, so every schedule
+  // sums the same partials in the same order (bitwise-equal results)
+  t.tile_in_slice = t.mt + t.ntile * mtc;
   t.gb = t.epi->b0 + t.lslice;
   t.lcoord = lbat ? t.gb : 0;
   t.rcoord = rbat ? t.gb : 0;
@@ -716,7 +727,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
       const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lslice, gb = ti_.gb;
       const int i = mt * BM + row;
-      if (p.prefetch_state) prefetch_tile_state(e, gb, mt, ntile, q, lane);
+      if (ti_.prefetch) prefetch_tile_state(e, gb, mt, ntile, q, lane);
       if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
         fail(abort_flag, err);
         break;

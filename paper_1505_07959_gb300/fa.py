@@ -29,7 +29,8 @@ SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_s
            "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
            "fa_batch_solve", "fa_batch_destroy", "fa_plan_set_learned", "fa_plan_learned_coefs",
            "fa_learned_records_scratch", "fa_learned_records", "fa_plan_set_recorder",
-           "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam"]
+           "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam",
+           "fa_batch_autotune", "fa_batch_tuning", "fa_plan_autotune", "fa_plan_tuning"]
 FA_COARSE_EULER, FA_COARSE_LEARNED = 0, 1
 FA_MLP_FEATURES, FA_MLP_HIDDEN, FA_MLP_COEFS, FA_MLP_PARAMS = 8, 128, 4, 18196
 FA_RECORD_DOUBLES = 32
@@ -102,6 +103,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_mlp_loss_grad": [dp, ctypes.c_int, dp, dp, dp, dp, sz, vp],
         "fa_mlp_adam": [dp, dp, dp, dp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                         ctypes.c_float, ctypes.c_float, vp],
+        "fa_batch_autotune": [vp, ctypes.POINTER(vp), ctypes.c_char_p],
+        "fa_plan_autotune": [vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -111,6 +114,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fa_status_string.restype = ctypes.c_char_p
     lib.fa_last_error.argtypes = []
     lib.fa_last_error.restype = ctypes.c_char_p
+    for name in ("fa_batch_tuning", "fa_plan_tuning"):
+        getattr(lib, name).argtypes = [vp]
+        getattr(lib, name).restype = ctypes.c_char_p
     lib.fa_launch_count.argtypes = []
     lib.fa_launch_count.restype = ctypes.c_ulonglong
     lib.fa_launch_count_reset.argtypes = []
@@ -231,6 +237,18 @@ def fa_batch_solve(h, dAs, dXs, iters, last_dx):
     px = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in dXs])
     return _check(load_library().fa_batch_solve(h, pa, px, iters, last_dx),
                   allow=(FA_OK, FA_ERR_NOT_CONVERGED))
+
+
+def fa_batch_autotune(h, dAs, cache_path=None):
+    cnt = len(dAs)
+    pa = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in dAs])
+    _check(load_library().fa_batch_autotune(h, pa, None if cache_path is None else cache_path.encode()))
+    return load_library().fa_batch_tuning(h).decode()
+
+
+def fa_plan_autotune(h):
+    _check(load_library().fa_plan_autotune(h))
+    return load_library().fa_plan_tuning(h).decode()
 
 
 def fa_batch_destroy(h):
@@ -376,6 +394,10 @@ class Plan:
         st = fa_parareal_solve_host(self.handle, A, X0, X, rep)
         return X, _report(rep, hist, st)
 
+    def autotune(self):
+        """Tune the tensor-core launch schedule (the matrix must be set); returns the account."""
+        return fa_plan_autotune(self.handle)
+
     def set_learned(self, params):
         """Install the coefficient network (float32 blob of FA_MLP_PARAMS values)."""
         self.params = self.torch.as_tensor(params, dtype=self.torch.float32).cuda().contiguous()
@@ -484,6 +506,10 @@ class Batch:
             DTYPES[dtype] if isinstance(dtype, str) else int(dtype), self.stream.cuda_stream)
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device="cuda")
         fa_batch_bind_workspace(self.handle, self.ws.data_ptr(), self.ws_bytes)
+
+    def autotune(self, As, cache_path=None):
+        """Tune the launch schedule on these matrices (see fa_batch_autotune); returns the account."""
+        return fa_batch_autotune(self.handle, [a.contiguous() for a in As], cache_path)
 
     def solve(self, As):
         """As: list of (n_i, n_i) float64 CUDA tensors.  Returns (list of X_i, iters, last_dx, status)."""
