@@ -71,13 +71,19 @@ typedef enum { FA_FLOW_INV = 0, FA_FLOW_EXP = 1, FA_FLOW_SQRT = 2 } fa_flow;
  *            x0y0 + x0y1 + x1y0.
  * FA_BF16X4  products x0y0 + x0y1 + x1y0 + x2y0 (left operand to three terms).
  * FA_BF16X6  every product xa yb with a + b <= 2.
- * All BF16 forms accumulate in float32 on the tensor cores (tcgen05). */
+ * All BF16 forms accumulate in float32 on the tensor cores (tcgen05).
+ * FA_FP8E4M3 (fine propagator of the square-root flow only) the RK4 stage operands as E4M3 with
+ *            one float32 scale per 128 x 128 tile (delayed scaling: 448 / (2 amax) of the same
+ *            tile one stage earlier, saturating conversion), float32 accumulation per 128-wide
+ *            k-block, rescaled by the two operand tiles' scales; the coarse propagator then runs
+ *            in float64 or a BF16 form (coarse_dtype). */
 typedef enum {
   FA_F64 = 0,
   FA_BF16 = 1,
   FA_BF16X3 = 2,
   FA_BF16X4 = 3,
-  FA_BF16X6 = 4
+  FA_BF16X6 = 4,
+  FA_FP8E4M3 = 5
 } fa_dtype;
 
 typedef struct {
@@ -90,7 +96,8 @@ typedef struct {
   int max_iters;      /* K: maximum parareal iterations (fine sweeps after Step 0), >= 0 */
   double tol;         /* stop when max_n ||dU_n||_F / ||U_n||_F < tol (0 = run all K) */
   int fine_dtype;     /* fa_dtype of F */
-  int coarse_dtype;   /* fa_dtype of G (FA_F64, or the same BF16 form as F) */
+  int coarse_dtype;   /* fa_dtype of G (FA_F64, or the same BF16 form as F; any BF16 form when F
+                         is FA_FP8E4M3) */
   int refine_steps;   /* refinement steps on the result (inverse: float64 Newton-Schulz; square
                          root: Newton with the Sylvester equation, see fa_refine); 0 = none */
   int coarse_kind;    /* fa_coarse_kind of G (FA_COARSE_EULER = the paper's forward Euler) */

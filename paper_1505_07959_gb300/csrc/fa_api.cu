@@ -154,6 +154,16 @@ struct fa_plan_s {
   void *rec_scratch = nullptr;
   size_t rec_scratch_bytes = 0;
 
+  // E4M3 fine operands (FA_FP8E4M3): bytes [N][n][ldp8] in L and R form, double-buffered by
+  // stage, and the per-tile scales [parity][inverse scale, amax][N][qT][qT]
+  bool fp8 = false;
+  int ldp8 = 0, qT = 0;
+  uint8_t *Yl8[2] = {nullptr, nullptr}, *Yr8[2] = {nullptr, nullptr};
+  float *qbuf = nullptr;
+  CUtensorMap tmYl8[2]{}, tmYr8[2]{};
+  float *qinv(int par) const { return qbuf + (static_cast<size_t>(par) * 2) * d.N * qT * qT; }
+  float *qamax(int par) const { return qbuf + (static_cast<size_t>(par) * 2 + 1) * d.N * qT * qT; }
+
   bool needs_l() const { return d.flow != FA_FLOW_EXP; }  // Y in L form (left factor)
 };
 
@@ -194,7 +204,16 @@ size_t carve(fa_plan_s *p, char *base) {
       p->a_lo = c.take<float>(nn);
     }
   }
-  if (p->mixed) {
+  if (p->fp8) {
+    p->x_hi = c.take<float>(N * nn);
+    p->x_lo = c.take<float>(N * nn);
+    p->acc = c.take<float>(N * nn);
+    for (int k = 0; k < 2; ++k) {
+      p->Yl8[k] = c.take<uint8_t>(N * static_cast<size_t>(d.n) * p->ldp8);
+      p->Yr8[k] = c.take<uint8_t>(N * static_cast<size_t>(d.n) * p->ldp8);
+    }
+    p->qbuf = c.take<float>(4 * N * static_cast<size_t>(p->qT) * p->qT);
+  } else if (p->mixed) {
     p->x_hi = c.take<float>(N * nn);
     p->x_lo = c.take<float>(N * nn);
     p->acc = c.take<float>(N * nn);
@@ -306,9 +325,33 @@ fa_status encode(CUtensorMap *m, void *base, int n, int ldp, int nslices, int nt
   return FA_OK;
 }
 
+// Tensor map over E4M3 operand bytes [nslices][n][ldp8] with a 128 x 128 box (128-byte rows).
+fa_status encode8(CUtensorMap *m, void *base, int n, int ldp8, int nslices) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_err(FA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[4] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n),
+                        static_cast<cuuint64_t>(nslices), 1};
+  cuuint64_t strides[3] = {static_cast<cuuint64_t>(ldp8),
+                           static_cast<cuuint64_t>(n) * ldp8,
+                           static_cast<cuuint64_t>(nslices) * n * ldp8};
+  cuuint32_t box[4] = {128, 128, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_err(FA_ERR_CUDA, "cuTensorMapEncodeTiled (E4M3) failed (%d)", (int)r);
+  return FA_OK;
+}
+
 fa_status encode_all(fa_plan_s *p) {
   const int n = p->d.n, ldp = p->ldp, N = p->d.N;
   const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (p->fp8) {
+    for (int k = 0; k < 2; ++k) {
+      FA_TRY(encode8(&p->tmYl8[k], p->Yl8[k], n, p->ldp8, N));
+      FA_TRY(encode8(&p->tmYr8[k], p->Yr8[k], n, p->ldp8, N));
+    }
+  }
   if (p->Lq) {
     // refinement operands are symmetric (or left factors): one row-major term map serves as
     // either operand (BM = BN)
@@ -318,7 +361,7 @@ fa_status encode_all(fa_plan_s *p) {
     FA_TRY(encode(&p->tmLpq, p->Lpq, n, ldp, 1, 3, p->strideS, TC_BM));
   }
   if (p->Aop) FA_TRY(encode(&p->tmA, p->Aop, n, ldp, 1, tl, p->strideA, TC_BM));
-  if (p->mixed) {
+  if (p->mixed && !p->fp8) {
     for (int k = 0; k < 2; ++k) {
       FA_TRY(encode(&p->tmYr[k], p->Yr[k], n, ldp, N, tr, p->strideY, TC_BN));
       if (p->Yl[k]) FA_TRY(encode(&p->tmYl[k], p->Yl[k], n, ldp, N, tl, p->strideY, TC_BM));
@@ -388,8 +431,64 @@ fa_status check_ready(const fa_plan_s *p, bool need_matrix) {
 
 // ---- fine sweep ------------------------------------------------------------------------------
 
+// The fine sweep with E4M3 stage operands (square-root flow).
+fa_status fine_sweep_fp8(fa_plan_s *p, const double *U, double *out, const double *g_old) {
+  const fa_problem_desc &d = p->d;
+  const int n = d.n, N = d.N, J = d.fine_steps;
+  const double h = d.T / static_cast<double>(N) / static_cast<double>(J);
+  FA_CUDA(fa::launch_load_state(U, N, n, p->ldp, p->x_hi, p->x_lo, nullptr, 0, 0, nullptr, 0, 0,
+                                p->stream));
+  FA_CUDA(fa::launch_fp8_load(U, N, n, p->ldp8, p->Yl8[0], p->Yr8[0], p->qamax(0), p->qinv(0),
+                              p->stream));
+  fa::PairSet one;
+  memset(&one, 0, sizeof(one));
+  one.npairs = 1;
+  one.terms_l = one.terms_r = 1;
+  int cur = 0;
+  for (int j = 0; j < J; ++j) {
+    for (int s = 1; s <= 4; ++s) {
+      const bool last = (j == J - 1 && s == 4);
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_STAGE;
+      e.stage = s;
+      e.last = last ? 1 : 0;
+      e.h = h;
+      e.ch = (s == 3) ? h : (s < 3 ? 0.5 * h : 0.0);
+      e.f_out = out;
+      e.g_old = g_old;
+      e.x_hi = p->x_hi;
+      e.x_lo = p->x_lo;
+      e.acc = p->acc;
+      e.a_hi = p->a_hi;
+      e.a_lo = p->a_lo;
+      if (!last) {
+        e.out_l8 = p->Yl8[cur ^ 1];
+        e.out_r8 = p->Yr8[cur ^ 1];
+        e.ldp8 = p->ldp8;
+        e.q_T = p->qT;
+        e.q_amax_in = p->qamax(cur);
+        e.q_inv_out = p->qinv(cur ^ 1);
+        e.q_amax_out = p->qamax(cur ^ 1);
+      }
+      TcGemmParams g = fa::tc_launch_params(n, N, 1, 1, one);
+      g.fp8 = 1;
+      g.kblocks = (n + 127) / 128;
+      g.idesc = fa::ptx::idesc_e4m3_f32(TC_BM, TC_BN);
+      g.q_inv_l = g.q_inv_r = p->qinv(cur);
+      g.q_T = p->qT;
+      if (p->tune_prefetch >= 0) g.prefetch_state = p->tune_prefetch;
+      if (p->tune_raster >= 0) g.raster = p->tune_raster;
+      g.epi = e;
+      FA_TRY(tc(p, p->tmYl8[cur], p->tmYr8[cur], g));
+      cur ^= 1;
+    }
+  }
+  return FA_OK;
+}
+
 // F on every slice: out = F(U_b) (g_old == null) or F(U_b) - g_old_b.
 fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g_old) {
+  if (p->fp8) return fine_sweep_fp8(p, U, out, g_old);
   const fa_problem_desc &d = p->d;
   const int n = d.n, N = d.N, J = d.fine_steps;
   const size_t nn = p->nn;
@@ -742,6 +841,7 @@ fa_status records(fa_plan_s *p, const double *U, const double *F, const double *
   const fa_problem_desc &d = p->d;
   if (d.flow == FA_FLOW_SQRT)
     return set_err(FA_ERR_UNSUPPORTED, "pair records are implemented for the inverse and exponential flows");
+  if (p->fp8) return set_err(FA_ERR_UNSUPPORTED, "pair records need a BF16 or float64 fine dtype");
   if (!scratch || scratch_bytes < records_scratch_bytes(p))
     return set_err(FA_ERR_WORKSPACE, "records scratch of %zu bytes < %zu needed", scratch_bytes,
                    records_scratch_bytes(p));
@@ -1213,13 +1313,19 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   if (!(d->tol >= 0.0)) return set_err(FA_ERR_ARG, "tol must be >= 0");
   if (d->flow < FA_FLOW_INV || d->flow > FA_FLOW_SQRT)
     return set_err(FA_ERR_ARG, "unknown flow %d", d->flow);
-  if (d->fine_dtype < FA_F64 || d->fine_dtype > FA_BF16X6)
+  if (d->fine_dtype < FA_F64 || d->fine_dtype > FA_FP8E4M3)
     return set_err(FA_ERR_ARG, "unknown fine dtype %d", d->fine_dtype);
-  if (d->coarse_dtype != FA_F64 && d->coarse_dtype != d->fine_dtype)
+  if (d->fine_dtype == FA_FP8E4M3) {
+    if (d->coarse_dtype < FA_F64 || d->coarse_dtype > FA_BF16X6)
+      return set_err(FA_ERR_ARG, "with FA_FP8E4M3 F the coarse dtype is FA_F64 or a BF16 form");
+  } else if (d->coarse_dtype != FA_F64 && d->coarse_dtype != d->fine_dtype) {
     return set_err(FA_ERR_ARG, "coarse dtype must be FA_F64 or the fine dtype");
+  }
   if (d->refine_steps < 0) return set_err(FA_ERR_ARG, "refine_steps must be >= 0");
   if (d->coarse_kind != FA_COARSE_EULER && d->coarse_kind != FA_COARSE_LEARNED)
     return set_err(FA_ERR_ARG, "unknown coarse kind %d", d->coarse_kind);
+  if (d->fine_dtype == FA_FP8E4M3 && d->flow != FA_FLOW_SQRT)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FP8E4M3 operands are implemented for the square-root flow");
   if (d->coarse_kind == FA_COARSE_LEARNED) {
     if (d->flow == FA_FLOW_SQRT)
       return set_err(FA_ERR_UNSUPPORTED,
@@ -1243,9 +1349,13 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   p->stream = static_cast<cudaStream_t>(stream);
   p->device = dev;
   p->num_sms = prop.multiProcessorCount;
-  p->mixed = is_mixed(d->fine_dtype);
+  p->fp8 = d->fine_dtype == FA_FP8E4M3;
+  p->mixed = is_mixed(d->fine_dtype) || p->fp8;
   p->cmixed = is_mixed(d->coarse_dtype);
-  p->ps = fa::pair_set(p->mixed ? d->fine_dtype : d->coarse_dtype);
+  p->ps = fa::pair_set(p->fp8 ? (p->cmixed ? d->coarse_dtype : FA_BF16)
+                              : (p->mixed ? d->fine_dtype : d->coarse_dtype));
+  p->ldp8 = (d->n + 15) / 16 * 16;
+  p->qT = (d->n + 127) / 128;
   p->ldp = (d->n + 7) / 8 * 8;
   p->nn = static_cast<size_t>(d->n) * d->n;
   p->learned = d->coarse_kind == FA_COARSE_LEARNED;
@@ -1845,6 +1955,10 @@ const char *fa_batch_tuning(fa_batch_t b) { return b ? b->tuning.c_str() : ""; }
 
 fa_status fa_plan_autotune(fa_plan_t p) {
   FA_TRY(check_ready(p, true));
+  if (p->fp8) {
+    p->tuning = "E4M3 operands: the default schedule";
+    return FA_OK;
+  }
   if (!p->mixed) {
     p->tuning = "float64 products: nothing to tune";
     return FA_OK;

@@ -61,6 +61,15 @@ struct EpiParams {
   // new operand output (mixed: BF16 terms; f64: row-major float64)
   __nv_bfloat16 *out_l, *out_r;
   double *out64;
+  // E4M3 operand output (FA_FP8E4M3 fine sweeps): bytes in L form and R form [slice][n][ldp8],
+  // quantised with one float32 scale per 128 x 128 tile of the operand (delayed scaling: the
+  // tile's scale is 448 / (2 amax) of the same tile of the previous operand); the epilogue
+  // records the new operand's per-tile amax and the inverse scales it used.  Tile arrays are
+  // [slice][T][T], T = ceil(n / 128).
+  uint8_t *out_l8, *out_r8;
+  int ldp8, q_T;
+  const float *q_amax_in;
+  float *q_inv_out, *q_amax_out;
   // fine sweep outputs (row-major float64): f_out = X (or X - g_old when g_old != 0)
   double *f_out;
   const double *g_old;
@@ -112,6 +121,10 @@ struct TcGemmParams {
   uint32_t idesc;   // tcgen05 instruction descriptor
   unsigned long long *prof;   // optional per-role cycle counters (diagnostics), may be null
   int raster;                 // uniform launches: 0 = M-tile fastest, 1 = N-tile fastest
+  int fp8;                    // 1: E4M3 operands (kind::f8f6f4, 128-element k-blocks), the drain
+                              // scales each k-block by the two operand tiles' inverse scales
+  const float *q_inv_l, *q_inv_r;   // [slice][T][T] inverse scales of L's and R's source matrix
+  int q_T;
   int prefetch_state;         // 1: the epilogue warps prefetch their tile's state into L2 while
                               // the tile's products run (pays where the epilogue dominates:
                               // one term pair; with six it competes with the operand feed)
@@ -162,6 +175,11 @@ cudaError_t launch_load_state(const double *U, int nb, int n, int ldp, float *x_
                               __nv_bfloat16 *out_l, int terms_l, size_t stride_l,
                               __nv_bfloat16 *out_r, int terms_r, size_t stride_r,
                               cudaStream_t s);
+// E4M3 operand of the first RK4 stage from U (float64 [nb][n][n]): per 128 x 128 tile the
+// amax of U, then bytes in L and R form quantised with scale 448 / (2 amax); writes amax and the
+// inverse scales ([nb][T][T]).
+cudaError_t launch_fp8_load(const double *U, int nb, int n, int ldp8, uint8_t *out_l,
+                            uint8_t *out_r, float *amax, float *inv, cudaStream_t s);
 // Sum per-tile partial norms in a fixed order: norms[b][2] = sum over tiles.
 cudaError_t launch_reduce_norms(const double *part, int nslices, int tiles_per_slice,
                                 double *norms, cudaStream_t s);

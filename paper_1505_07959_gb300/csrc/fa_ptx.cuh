@@ -118,6 +118,17 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// D (TMEM, float32) (+)= A * B^T with 8-bit float operands (both E4M3 here) from shared memory;
+// one instruction covers K = 32 elements (32 bytes of each operand row, as K = 16 BF16 do).
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
 // Arrive on `bar` once every tcgen05 operation issued so far by this thread completes.
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
   asm volatile(
@@ -188,17 +199,23 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 // Instruction descriptor of tcgen05.mma kind::f16: float32 accumulator
 // (bits 4-5 = 1), BF16 A and B (bits 7-9 = 1, 10-12 = 1), both K-major
 // (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (type code 0) and float32 D.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-// True on exactly one (the same) active lane of a converged warp.
 // Bring the 128-byte line holding `ptr` into L2 (no register result, no ordering).
 __device__ __forceinline__ void prefetch_l2(const void *ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
+// True on exactly one (the same) active lane of a converged warp.
 __device__ __forceinline__ bool elect_one() {
   uint32_t pred = 0;
   asm volatile(

@@ -34,6 +34,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fa_internal.h"
 #include "fa_ptx.cuh"
@@ -152,9 +153,9 @@ __device__ __forceinline__ void put_l1(const EpiParams &e, size_t off, const Ter
 // Writes the next stage operand Y_{s+1} in R and L form; on the slice's last step
 // writes F (or F - G_old) in float64 row-major instead.  Columns go in groups of
 // 16 whose state loads are issued before any of them is used.
-template <int STAGE, bool SQRT, bool LAST>
+template <int STAGE, bool SQRT, bool LAST, bool Q8 = false>
 __device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, int j0, int cnt,
-                                            const float (&v)[32]) {
+                                            const float (&v)[32], float s8, float &amx) {
   constexpr int GW = 16;
   const int n = e.n;
   const size_t nn = static_cast<size_t>(n) * n;
@@ -215,6 +216,34 @@ __device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, in
           const double X = static_cast<double>(xh[u]) + static_cast<double>(xl[u]);
           e.f_out[r0 + u] = e.g_old ? X - e.g_old[r0 + u] : X;
         }
+      }
+      continue;
+    }
+    if (Q8) {
+      // E4M3 operand: quantised with the tile's scale, L form (16 bytes) and R form bytes
+      uint8_t q8[GW];
+#pragma unroll
+      for (int u = 0; u < GW; ++u) {
+        const float y = u < gcnt ? xh[u] : 0.0f;
+        amx = fmaxf(amx, fabsf(y));
+        q8[u] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(y * s8, __NV_SATFINITE, __NV_E4M3));
+      }
+#pragma unroll
+      for (int u = 0; u < GW; ++u)
+        if (u < gcnt)
+          e.out_r8[(static_cast<size_t>(b) * n + j0 + GW * g + u) * e.ldp8 + i] = q8[u];
+      const size_t off = (static_cast<size_t>(b) * n + i) * e.ldp8 + j0 + GW * g;
+      if (gcnt == GW) {
+        uint4 w;
+        w.x = q8[0] | (q8[1] << 8) | (q8[2] << 16) | (static_cast<uint32_t>(q8[3]) << 24);
+        w.y = q8[4] | (q8[5] << 8) | (q8[6] << 16) | (static_cast<uint32_t>(q8[7]) << 24);
+        w.z = q8[8] | (q8[9] << 8) | (q8[10] << 16) | (static_cast<uint32_t>(q8[11]) << 24);
+        w.w = q8[12] | (q8[13] << 8) | (q8[14] << 16) | (static_cast<uint32_t>(q8[15]) << 24);
+        *reinterpret_cast<uint4 *>(e.out_l8 + off) = w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < GW; ++u)
+          if (u < gcnt) e.out_l8[off + u] = q8[u];
       }
       continue;
     }
@@ -477,6 +506,7 @@ __device__ __forceinline__ void fail(volatile int *abort_flag, int *err) {
 }
 
 // 10 warps: at most three per SM sub-partition, so up to 168 registers per thread.
+template <bool FP8>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmL,
                    const __grid_constant__ CUtensorMap tmR,
@@ -544,6 +574,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         term[t] = p.tl_term[t];
       }
       const int ntl = p.ntl;
+      constexpr int bke = FP8 ? 2 * BK : BK;   // k-block width in elements (128 bytes per row)
       uint32_t g = 0, k = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
@@ -566,9 +597,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (ti == 0) ptx::mbar_arrive_expect_tx(fb, ntl * TILE_BYTES);
             uint8_t *dst = smem + (gt % NSLOT) * TILE_BYTES;
             if (side[ti] == 0)
-              ptx::tma_load_4d(dst, ti_.tmL, fb, kb * BK, mt * BM, lb, term[ti]);
+              ptx::tma_load_4d(dst, ti_.tmL, fb, kb * bke, mt * BM, lb, term[ti]);
             else
-              ptx::tma_load_4d(dst, ti_.tmR, fb, kb * BK, ntile * BN, rb, term[ti]);
+              ptx::tma_load_4d(dst, ti_.tmR, fb, kb * bke, ntile * BN, rb, term[ti]);
           }
           g += ntl;
         }
@@ -591,6 +622,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       const int npairs = p.npairs, ntl = p.ntl;
       const uint32_t idesc = p.idesc;
+      constexpr bool fp8 = FP8;
       const uint64_t desc0 = ptx::sdesc_sw128(ptx::smem_u32(smem));
       uint32_t g = 0, k = 0;
       int mb = 0;
@@ -625,7 +657,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int kk = 0; kk < BK / 16; ++kk) {
                   // K-step kk starts 32 bytes further into the 128-byte swizzled rows.
                   const uint32_t acc = (q == 0) ? (kk > 0) : (kb > 0 || q > 1 || kk > 0);
-                  ptx::tc_mma_bf16(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
+                  if (fp8)
+                    ptx::tc_mma_f8(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
+                  else
+                    ptx::tc_mma_bf16(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
                 }
                 if (q == 0) ptx::tc_commit(mbfull + mb);
               }
@@ -652,7 +687,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t mph = 0, cph = 0, fph = 0;
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
-      const int kblocks = tile_info(p, &tmL, &tmR, tile).kblocks;
+      const TileInfo tix = tile_info(p, &tmL, &tmR, tile);
+      const int kblocks = tix.kblocks;
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
@@ -664,12 +700,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         ptx::tc_fence_after();
         const long long td = clock64();
+        // E4M3 operands: undo the two tiles' scales of this k-block (L tile (mt, kb) of its
+        // source matrix, R tile (ntile, kb) of the transposed source, i.e. its tile (kb, ntile));
+        // f = 1 for BF16 terms, where fma(v, 1, acc) is the plain sum
+        float f = 1.0f;
+        if constexpr (FP8) {
+          const int T = p.q_T;
+          f = p.q_inv_l[(static_cast<size_t>(tix.lcoord) * T + tix.mt) * T + kb] *
+              p.q_inv_r[(static_cast<size_t>(tix.rcoord) * T + kb) * T + tix.ntile];
+        }
 #pragma unroll
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
           ptx::tmem_ld_32x32b_x32(lane_base + MB_COL0 + static_cast<uint32_t>(mb * BN + c * 32), v);
 #pragma unroll
-          for (int u = 0; u < 32; ++u) acc[c * 32 + u] += v[u];
+          for (int u = 0; u < 32; ++u) acc[c * 32 + u] = fmaf(v[u], f, acc[c * 32 + u]);
         }
         if (prof) atomicAdd(prof + 9, static_cast<unsigned long long>(clock64() - td));
         ptx::tc_fence_before();
@@ -735,6 +780,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::tc_fence_after();
       const long long ts = clock64();
       double s0 = 0.0, s1 = 0.0;
+      // E4M3 operand output: the tile's scale from the previous operand's amax (delayed scaling)
+      const bool q8 = FP8 && e.mode == EPI_STAGE && e.out_l8 != nullptr && !e.last;
+      float s8 = 1.0f, amx = 0.0f;
+      size_t qslot = 0;
+      if (q8) {
+        qslot = (static_cast<size_t>(gb) * e.q_T + mt) * e.q_T + ntile;
+        const float a = e.q_amax_in[qslot];
+        s8 = a > 0.0f ? 224.0f / a : 1.0f;        // 448 / (2 amax): one binade of headroom
+      }
       for (int c = 0; c < BN / 32; ++c) {
         const int j0 = ntile * BN + c * 32;
         float v[32];
@@ -743,21 +797,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int cnt = (n - j0) < 32 ? (n - j0) : 32;
         if (e.mode == EPI_STAGE) {
           const bool sq = e.flow == FA_FLOW_SQRT;
+          if constexpr (FP8) {
+            // E4M3 operands exist for the square-root flow only; the last stage writes F
+            if (q8) {
+              switch (e.stage) {
+                case 1: stage_chunk<1, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                case 2: stage_chunk<2, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                case 3: stage_chunk<3, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                default: stage_chunk<4, true, false, true>(e, gb, i, j0, cnt, v, s8, amx);
+              }
+            } else {
+              stage_chunk<4, true, true>(e, gb, i, j0, cnt, v, s8, amx);
+            }
+          } else {
           switch (e.stage) {
-            case 1: sq ? stage_chunk<1, true, false>(e, gb, i, j0, cnt, v)
-                       : stage_chunk<1, false, false>(e, gb, i, j0, cnt, v); break;
-            case 2: sq ? stage_chunk<2, true, false>(e, gb, i, j0, cnt, v)
-                       : stage_chunk<2, false, false>(e, gb, i, j0, cnt, v); break;
-            case 3: sq ? stage_chunk<3, true, false>(e, gb, i, j0, cnt, v)
-                       : stage_chunk<3, false, false>(e, gb, i, j0, cnt, v); break;
+            case 1: sq ? stage_chunk<1, true, false>(e, gb, i, j0, cnt, v, s8, amx)
+                       : stage_chunk<1, false, false>(e, gb, i, j0, cnt, v, s8, amx); break;
+            case 2: sq ? stage_chunk<2, true, false>(e, gb, i, j0, cnt, v, s8, amx)
+                       : stage_chunk<2, false, false>(e, gb, i, j0, cnt, v, s8, amx); break;
+            case 3: sq ? stage_chunk<3, true, false>(e, gb, i, j0, cnt, v, s8, amx)
+                       : stage_chunk<3, false, false>(e, gb, i, j0, cnt, v, s8, amx); break;
             default:
               if (e.last) {
-                sq ? stage_chunk<4, true, true>(e, gb, i, j0, cnt, v)
-                   : stage_chunk<4, false, true>(e, gb, i, j0, cnt, v);
+                sq ? stage_chunk<4, true, true>(e, gb, i, j0, cnt, v, s8, amx)
+                   : stage_chunk<4, false, true>(e, gb, i, j0, cnt, v, s8, amx);
               } else {
-                sq ? stage_chunk<4, true, false>(e, gb, i, j0, cnt, v)
-                   : stage_chunk<4, false, false>(e, gb, i, j0, cnt, v);
+                sq ? stage_chunk<4, true, false>(e, gb, i, j0, cnt, v, s8, amx)
+                   : stage_chunk<4, false, false>(e, gb, i, j0, cnt, v, s8, amx);
               }
+          }
           }
         } else if (e.mode == EPI_PROD) {
 #pragma unroll
@@ -777,6 +845,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (prof) {
         atomicAdd(prof + 8, static_cast<unsigned long long>(clock64() - ts));
         atomicAdd(prof + 11, 1ull);
+      }
+      if (FP8 && q8) {
+        // the new operand tile's amax (for the next stage's scale) and the scale this one used
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+        if (lane == 0) red[sw] = static_cast<double>(amx);
+        ptx::named_bar_sync(2, STORE_WARPS * 32);
+        if (sw == 0 && lane == 0) {
+          double m = red[0];
+          for (int w = 1; w < STORE_WARPS; ++w) m = fmax(m, red[w]);
+          e.q_amax_out[qslot] = static_cast<float>(m);
+          e.q_inv_out[qslot] = 1.0f / s8;
+        }
+        ptx::named_bar_sync(2, STORE_WARPS * 32);
       }
       if (norms) {
 #pragma unroll
@@ -970,18 +1052,26 @@ PairSet pair_set(int dtype) {
 
 cudaError_t launch_tc_gemm(const CUtensorMap *tmL, const CUtensorMap *tmR, const TcGemmParams &p,
                            int num_sms, cudaStream_t s) {
-  static thread_local int attr_set_for = -1;
+  static thread_local int attr_set_for[2] = {-1, -1};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (attr_set_for != dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(SMEM_BYTES));
+  const int v = p.fp8 ? 1 : 0;
+  if (attr_set_for[v] != dev) {
+    cudaError_t e = v ? cudaFuncSetAttribute(tc_gemm_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(SMEM_BYTES))
+                      : cudaFuncSetAttribute(tc_gemm_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(SMEM_BYTES));
     if (e != cudaSuccess) return e;
-    attr_set_for = dev;
+    attr_set_for[v] = dev;
   }
   if (p.num_tiles <= 0) return cudaSuccess;
   const int grid = p.num_tiles < num_sms ? p.num_tiles : num_sms;
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(*tmL, *tmR, p);
+  if (v)
+    tc_gemm_kernel<true><<<grid, THREADS, SMEM_BYTES, s>>>(*tmL, *tmR, p);
+  else
+    tc_gemm_kernel<false><<<grid, THREADS, SMEM_BYTES, s>>>(*tmL, *tmR, p);
   count_launch();
   return cudaGetLastError();
 }
@@ -995,6 +1085,77 @@ cudaError_t launch_tc_gemm_ragged(const TcSegment *segs, int nseg, int num_tiles
   CUtensorMap unused;
   memset(&unused, 0, sizeof(unused));
   return launch_tc_gemm(&unused, &unused, q, num_sms, s);
+}
+
+namespace {
+
+// amax of every 128 x 128 tile of U (float64 [nb][n][n]); grid (T, T, nb), 256 threads.
+__global__ void __launch_bounds__(256) tile_amax_kernel(const double *__restrict__ U, int n, int T,
+                                                        float *amax) {
+  const int tc = blockIdx.x, tr = blockIdx.y, b = blockIdx.z;
+  const double *S = U + static_cast<size_t>(b) * n * n;
+  float m = 0.0f;
+  for (int idx = threadIdx.x; idx < 128 * 128; idx += 256) {
+    const int i = tr * 128 + idx / 128, j = tc * 128 + idx % 128;
+    if (i < n && j < n) m = fmaxf(m, static_cast<float>(fabs(S[static_cast<size_t>(i) * n + j])));
+  }
+  __shared__ float red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = red[0];
+    for (int w = 1; w < 8; ++w) r = fmaxf(r, red[w]);
+    amax[(static_cast<size_t>(b) * T + tr) * T + tc] = r;
+  }
+}
+
+// E4M3 bytes of U in L form and R form with the per-tile scale 448 / (2 amax) (32 x 32 blocks,
+// the R form through a shared-memory transpose); the block at a 128-tile's corner records the
+// inverse scale.
+__global__ void fp8_quant_kernel(const double *__restrict__ U, int n, int ldp8, int T,
+                                 const float *__restrict__ amax, uint8_t *out_l, uint8_t *out_r,
+                                 float *inv) {
+  __shared__ uint8_t tile[TT][TT + 4];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const size_t slot = (static_cast<size_t>(b) * T + i0 / 128) * T + j0 / 128;
+  const float a = amax[slot];
+  const float s = a > 0.0f ? 224.0f / a : 1.0f;
+  if (tx == 0 && ty == 0 && i0 % 128 == 0 && j0 % 128 == 0) inv[slot] = 1.0f / s;
+  const double *S = U + static_cast<size_t>(b) * n * n;
+  for (int r = ty; r < TT; r += 8) {
+    const int i = i0 + r, j = j0 + tx;
+    uint8_t q = 0;
+    if (i < n && j < n) {
+      q = static_cast<uint8_t>(__nv_cvt_float_to_fp8(
+          static_cast<float>(S[static_cast<size_t>(i) * n + j]) * s, __NV_SATFINITE, __NV_E4M3));
+      out_l[(static_cast<size_t>(b) * n + i) * ldp8 + j] = q;
+    }
+    tile[r][tx] = q;
+  }
+  __syncthreads();
+  for (int r = ty; r < TT; r += 8) {
+    const int j = j0 + r, i = i0 + tx;
+    if (i < n && j < n) out_r[(static_cast<size_t>(b) * n + j) * ldp8 + i] = tile[tx][r];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fp8_load(const double *U, int nb, int n, int ldp8, uint8_t *out_l,
+                            uint8_t *out_r, float *amax, float *inv, cudaStream_t s) {
+  const int T = (n + 127) / 128;
+  tile_amax_kernel<<<dim3(T, T, nb), 256, 0, s>>>(U, n, T, amax);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid((n + TT - 1) / TT, (n + TT - 1) / TT, nb), block(TT, 8);
+  fp8_quant_kernel<<<grid, block, 0, s>>>(U, n, ldp8, T, amax, out_l, out_r, inv);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_split_terms(const double *src, int nb, int n, int ldp, __nv_bfloat16 *out_l,

@@ -20,9 +20,9 @@ LIB_PATH = os.path.join(HERE, "libfa.so")
 FA_OK = 0
 FA_ERR_NOT_CONVERGED = 5
 FA_FLOW_INV, FA_FLOW_EXP, FA_FLOW_SQRT = 0, 1, 2
-FA_F64, FA_BF16, FA_BF16X3, FA_BF16X4, FA_BF16X6 = 0, 1, 2, 3, 4
+FA_F64, FA_BF16, FA_BF16X3, FA_BF16X4, FA_BF16X6, FA_FP8E4M3 = 0, 1, 2, 3, 4, 5
 DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16X4,
-          "bf16x6": FA_BF16X6}
+          "bf16x6": FA_BF16X6, "fp8e4m3": FA_FP8E4M3}
 SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_sweep",
            "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
            "fa_debug_product", "fa_debug_set_profile", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
