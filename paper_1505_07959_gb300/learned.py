@@ -8,7 +8,10 @@ Data.  Every training matrix is A = Q diag(lam) Q^T of the wide-spectrum inverse
 generates the trajectories: a parareal solve (fa_parareal_solve, coarse propagator the degree-4
 Taylor step, i.e. the constant network c = (1, 1, 1, 1)) runs `gen_iters` iterations with the
 plan's pair recorder on, so every fine sweep adds the N pairs (U^k_n, F(U^k_n)) as records
-(features + 4 x 4 Gram data, computed on the GPU).
+(features + 4 x 4 Gram data, computed on the GPU).  A second round (--gen-weights) generates
+records with a trained network as the coarse propagator, so that the training set also holds
+the states that network's own solves visit (the late slices' states of a Taylor-4 solve are far
+from them), and trains on the union (--records-in adds earlier records).
 
 Training.  Feature standardisation (mu, sd) from the training records; network initialised with
 He-scaled hidden layers, W3 = 0 and b3 = (1, 1, 1, 1) (the Taylor step); Adam on minibatches of
@@ -99,14 +102,16 @@ def init_blob(mu, sd, seed: int, c0=(1.0, 1.0, 1.0, 1.0)) -> np.ndarray:
     return p
 
 
-def generate(cfg: TrainConfig, log=None) -> np.ndarray:
-    """Pair records (host float64 (R, FA_RECORD_DOUBLES)) from the method's own solves."""
+def generate(cfg: TrainConfig, log=None, gen_blob=None) -> np.ndarray:
+    """Pair records (host float64 (R, FA_RECORD_DOUBLES)) from the method's own solves; the
+    generating solves use the Taylor-4 step, or the network `gen_blob` when given (records of
+    the iterates that network's own solves visit)."""
     import torch
 
     build.build_library()
     fa.load_library()
     out = []
-    taylor = constant_blob((1.0, 1.0, 1.0, 1.0))
+    taylor = constant_blob((1.0, 1.0, 1.0, 1.0)) if gen_blob is None else np.asarray(gen_blob, dtype=np.float32)
     plans = {}
     t0 = time.time()
     for i, seed in enumerate(cfg.seeds):
@@ -247,6 +252,11 @@ def main() -> None:
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--dtype", default="bf16x6")
     t.add_argument("--log", default=None, help="JSON summary file")
+    t.add_argument("--gen-weights", default=None, help="network blob for the generating solves")
+    t.add_argument("--records-in", action="append", default=[], help=".npy records to add")
+    t.add_argument("--records-out", default=None, help="save the generated records (.npy)")
+    t.add_argument("--seed0", type=int, default=0, help="first training matrix seed")
+    t.add_argument("--train-only", action="store_true", help="no generation: train on --records-in")
     e = sub.add_parser("evaluate")
     e.add_argument("--weights", default=DEFAULT_WEIGHTS)
     e.add_argument("--n", type=int, default=1024)
@@ -261,20 +271,29 @@ def main() -> None:
     e.add_argument("--log", default=None, help="JSON summary file")
     a = ap.parse_args()
     if a.cmd == "train":
-        ns = log_uniform_sizes(a.trajectories, a.n_lo, a.n_hi, 12345)
-        # sizes rounded to multiples of 8 keep the plans few (one per distinct order)
+        ns = log_uniform_sizes(a.trajectories, a.n_lo, a.n_hi, 12345 + a.seed0)
+        # sizes rounded to multiples of 32 keep the plans few (one per distinct order)
         ns = [max(8, int(round(x / 32)) * 32) for x in ns]
-        cfg = TrainConfig(ns=ns, seeds=range(a.trajectories), N=a.N, J=a.J, dtype=a.dtype,
-                          gen_iters=a.gen_iters, steps=a.steps, batch=a.batch, lr=a.lr)
+        cfg = TrainConfig(ns=ns, seeds=range(a.seed0, a.seed0 + a.trajectories), N=a.N, J=a.J,
+                          dtype=a.dtype, gen_iters=a.gen_iters, steps=a.steps, batch=a.batch,
+                          lr=a.lr)
         t0 = time.time()
-        recs = generate(cfg, log=print)
+        parts = [np.load(f) for f in a.records_in]
+        if not a.train_only:
+            gen_blob = None if a.gen_weights is None else np.fromfile(a.gen_weights, dtype=np.float32)
+            new = generate(cfg, log=print, gen_blob=gen_blob)
+            if a.records_out:
+                np.save(a.records_out, new)
+            parts.append(new)
+        recs = np.concatenate(parts, axis=0)
         t1 = time.time()
-        print(f"{recs.shape[0]} records from {a.trajectories} trajectories in {t1 - t0:.1f} s")
+        print(f"{recs.shape[0]} records ({a.trajectories if not a.train_only else 0} new trajectories) in {t1 - t0:.1f} s")
         params, hist = train(recs, cfg, log=print)
         t2 = time.time()
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         params.astype(np.float32).tofile(a.out)
-        summary = {"trajectories": a.trajectories, "n_range": [a.n_lo, a.n_hi], "N": a.N,
+        summary = {"trajectories": a.trajectories, "records_in": a.records_in,
+                   "gen_weights": a.gen_weights, "n_range": [a.n_lo, a.n_hi], "N": a.N,
                    "J": a.J, "dtype": a.dtype, "gen_iters": a.gen_iters, "records": int(recs.shape[0]),
                    "gen_s": t1 - t0, "train_s": t2 - t1, "steps": a.steps, "batch": a.batch,
                    "loss_first": hist[0], "loss_final_full": hist[-1]}
