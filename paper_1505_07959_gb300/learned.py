@@ -8,7 +8,7 @@ Data.  Every training matrix is A = Q diag(lam) Q^T of the wide-spectrum inverse
 generates the trajectories: a parareal solve (fa_parareal_solve, coarse propagator the degree-4
 Taylor step, i.e. the constant network c = (1, 1, 1, 1)) runs `gen_iters` iterations with the
 plan's pair recorder on, so every fine sweep adds the N pairs (U^k_n, F(U^k_n)) as records
-(features + 4 x 4 Gram data, computed on the GPU).  A second round (--gen-weights) generates
+(features + 4 x 4 Gram data, computed on the GPU).  A second pass (--gen-weights) generates
 records with a trained network as the coarse propagator, so that the training set also holds
 the states that network's own solves visit (the late slices' states of a Taylor-4 solve are far
 from them), and trains on the union (--records-in adds earlier records).
@@ -268,6 +268,8 @@ def main() -> None:
     e.add_argument("--dtype", default="bf16x6")
     e.add_argument("--coarse-dtype", default="f64")
     e.add_argument("--refine", type=int, default=2)
+    e.add_argument("--kinds", default="euler,taylor4,learned",
+                   help="comma-separated coarse propagators to solve with")
     e.add_argument("--log", default=None, help="JSON summary file")
     a = ap.parse_args()
     if a.cmd == "train":
@@ -302,10 +304,13 @@ def main() -> None:
             with open(a.log, "w") as f:
                 json.dump({"summary": summary, "loss_history": hist}, f)
     else:
+        kinds = tuple(a.kinds.split(","))
+        if not kinds or not set(kinds) <= {"euler", "taylor4", "learned"}:
+            ap.error("--kinds takes euler, taylor4 and learned")
         params = np.fromfile(a.weights, dtype=np.float32)
         res = evaluate(params, ns=(a.n,), seeds=range(a.seed0, a.seed0 + a.seeds), N=a.N, J=a.J,
                        tol=a.tol, dtype=a.dtype, coarse_dtype=a.coarse_dtype,
-                       refine_steps=a.refine, log=print)
+                       kinds=kinds, refine_steps=a.refine, log=print)
         s = summarise(res)
         print(json.dumps(s))
         if a.log:
