@@ -387,13 +387,41 @@ __device__ __forceinline__ void store_chunk(const EpiParams &e, int b, int i, in
   if (e.terms_r || e.terms_l) write_terms(e, b, i, j0, cnt, w);
 }
 
+// In one-term launches the drain warps wait for the finished-tile buffer for about half of each
+// tile, so for the square-root flow's RK4 stages they form K = (A_hi - P) + A_lo themselves (the
+// same float32 operations as the epilogue would do, so the same bits): the epilogue, which bounds
+// these launches, then reads two fewer arrays per element.  Measured, this pays up to n = 2048;
+// at n = 4096 A's tile no longer stays in L2 from the tile's start to the end of its products,
+// and the drain's latency-bound loads of it lengthen the tile more than the epilogue gains.
+__device__ __forceinline__ bool drain_forms_k(const TcGemmParams &p, const EpiParams &e) {
+  return p.npairs == 1 && e.mode == EPI_STAGE && e.flow == FA_FLOW_SQRT && e.n <= 2048;
+}
+
+// L2 prefetch of A's float32 pair over the 32 rows i0.. and the tile's 128 columns (one 32-row
+// segment, at most two lines, per column; lane + 32 k columns per lane).
+__device__ __forceinline__ void prefetch_a_pair(const EpiParams &e, int i0, int ntile, int lane) {
+  const int n = e.n;
+  if (i0 >= n) return;
+  const int last = n - 1 - i0 < 31 ? n - 1 - i0 : 31;
+#pragma unroll
+  for (int k = 0; k < BN / 32; ++k) {
+    const int j = ntile * BN + lane + 32 * k;
+    if (j >= n) break;
+    const size_t c = static_cast<size_t>(j) * n + i0;
+    ptx::prefetch_l2(e.a_hi + c);
+    ptx::prefetch_l2(e.a_hi + c + last);
+    ptx::prefetch_l2(e.a_lo + c);
+    ptx::prefetch_l2(e.a_lo + c + last);
+  }
+}
+
 // Prefetch into L2 the state that the epilogue of tile (mt, ntile) of slice b will read, for the
 // 32 rows of this warp's TMEM lane quarter: issued while the store warps wait for the tile's
 // products, it turns the epilogue's dependent HBM loads into L2 hits.  Column-major state (RK4
 // stage arrays, A's float32 pair): one 32-row segment (<= two lines) per column, lane + 32 k
 // columns per lane; row-major state (Euler / store addends): the row's 128 columns.
 __device__ __forceinline__ void prefetch_tile_state(const EpiParams &e, int b, int mt, int ntile,
-                                                    int q, int lane) {
+                                                    int q, int lane, bool skip_a) {
   const int n = e.n;
   const int i0 = mt * BM + q * 32;
   if (i0 >= n) return;
@@ -401,8 +429,8 @@ __device__ __forceinline__ void prefetch_tile_state(const EpiParams &e, int b, i
   if (e.mode == EPI_STAGE) {
     const int last = n - 1 - i0 < 31 ? n - 1 - i0 : 31;     // last row of the segment inside n
     const float *arr[5] = {e.x_hi, e.stage > 1 ? e.acc : nullptr, e.stage == 4 ? e.x_lo : nullptr,
-                           e.flow == FA_FLOW_SQRT ? e.a_hi : nullptr,
-                           e.flow == FA_FLOW_SQRT ? e.a_lo : nullptr};
+                           e.flow == FA_FLOW_SQRT && !skip_a ? e.a_hi : nullptr,
+                           e.flow == FA_FLOW_SQRT && !skip_a ? e.a_lo : nullptr};
 #pragma unroll
     for (int k = 0; k < BN / 32; ++k) {
       const int j = ntile * BN + lane + 32 * k;
@@ -689,6 +717,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
       const TileInfo tix = tile_info(p, &tmL, &tmR, tile);
       const int kblocks = tix.kblocks;
+      const bool form_k = drain_forms_k(p, *tix.epi);
+      if (form_k) prefetch_a_pair(*tix.epi, tix.mt * BM + q * 32, tix.ntile, lane);
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
@@ -740,17 +770,63 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::tc_fence_before();
       ptx::mbar_arrive(cbempty);
       cph ^= 1u;
+      if (form_k) {
+        // K = (A_hi - P) + A_lo for row i, formed in the correction buffer (no MMA writes it in
+        // one-term launches) 32 columns at a time, so that only one chunk is held in registers
+        const EpiParams &e = *tix.epi;
+        const int n = e.n;
+        const int i = tix.mt * BM + q * 32 + lane;
+        const int jb = tix.ntile * BN;
+#pragma unroll
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+#pragma unroll
+          for (int u = 0; u < 32; ++u) v[u] = acc[c * 32 + u];
+          ptx::tmem_st_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
+        }
+        ptx::tmem_wait_st();
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          ptx::tmem_ld_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
+          if (i < n) {
+#pragma unroll
+            for (int h = 0; h < 32; h += 8) {
+              float ah[8], al[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int j = jb + c * 32 + h + u;
+                const size_t ca = static_cast<size_t>(j < n ? j : 0) * n + i;
+                ah[u] = j < n ? e.a_hi[ca] : 0.0f;
+                al[u] = j < n ? e.a_lo[ca] : 0.0f;
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (jb + c * 32 + h + u < n) v[h + u] = (ah[u] - v[h + u]) + al[u];
+            }
+          }
+          ptx::tmem_st_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
+        }
+        ptx::tmem_wait_st();
+      }
       if (!pwait(finempty, fph ^ 1u, abort_flag, prof, 6, 100)) {
         fail(abort_flag, err);
         break;
       }
       ptx::tc_fence_after();
+      if (form_k) {
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          ptx::tmem_ld_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
+          ptx::tmem_st_32x32b_x32(lane_base + FIN_COL + static_cast<uint32_t>(c * 32), v);
+        }
+      } else {
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = acc[c * 32 + u];
-        ptx::tmem_st_32x32b_x32(lane_base + FIN_COL + static_cast<uint32_t>(c * 32), v);
+          for (int u = 0; u < 32; ++u) v[u] = acc[c * 32 + u];
+          ptx::tmem_st_32x32b_x32(lane_base + FIN_COL + static_cast<uint32_t>(c * 32), v);
+        }
       }
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
@@ -772,7 +848,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
       const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lslice, gb = ti_.gb;
       const int i = mt * BM + row;
-      if (ti_.prefetch) prefetch_tile_state(e, gb, mt, ntile, q, lane);
+      const bool kform = drain_forms_k(p, e);   // the finished tile holds K, not the product
+      if (ti_.prefetch) prefetch_tile_state(e, gb, mt, ntile, q, lane, kform);
       if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
         fail(abort_flag, err);
         break;
@@ -796,16 +873,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (j0 >= n || i >= n) continue;
         const int cnt = (n - j0) < 32 ? (n - j0) : 32;
         if (e.mode == EPI_STAGE) {
-          const bool sq = e.flow == FA_FLOW_SQRT;
+          // the square-root flow's K = A - P, unless the drain formed it already
+          const bool sq = e.flow == FA_FLOW_SQRT && !kform;
           if constexpr (FP8) {
-            // E4M3 operands exist for the square-root flow only; the last stage writes F
-            if (q8) {
+            // E4M3 operands exist for the square-root flow only (one term, so the drain forms
+            // K); the last stage writes F
+            if (q8 && !sq) {
+              switch (e.stage) {
+                case 1: stage_chunk<1, false, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                case 2: stage_chunk<2, false, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                case 3: stage_chunk<3, false, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
+                default: stage_chunk<4, false, false, true>(e, gb, i, j0, cnt, v, s8, amx);
+              }
+            } else if (q8) {
               switch (e.stage) {
                 case 1: stage_chunk<1, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
                 case 2: stage_chunk<2, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
                 case 3: stage_chunk<3, true, false, true>(e, gb, i, j0, cnt, v, s8, amx); break;
                 default: stage_chunk<4, true, false, true>(e, gb, i, j0, cnt, v, s8, amx);
               }
+            } else if (!sq) {
+              stage_chunk<4, false, true>(e, gb, i, j0, cnt, v, s8, amx);
             } else {
               stage_chunk<4, true, true>(e, gb, i, j0, cnt, v, s8, amx);
             }
