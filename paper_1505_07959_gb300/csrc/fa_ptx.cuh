@@ -215,6 +215,11 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
+// The same with the evict-last priority: the line stays in L2 ahead of streamed data.
+__device__ __forceinline__ void prefetch_l2_keep(const void *ptr) {
+  asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(ptr));
+}
+
 // True on exactly one (the same) active lane of a converged warp.
 __device__ __forceinline__ bool elect_one() {
   uint32_t pred = 0;

@@ -398,7 +398,8 @@ __device__ __forceinline__ bool drain_forms_k(const TcGemmParams &p, const EpiPa
 }
 
 // L2 prefetch of A's float32 pair over the 32 rows i0.. and the tile's 128 columns (one 32-row
-// segment, at most two lines, per column; lane + 32 k columns per lane).
+// segment, at most two lines, per column; lane + 32 k columns per lane), with the evict-last
+// priority: the RK4 state streaming through L2 during the tile's products would evict it first.
 __device__ __forceinline__ void prefetch_a_pair(const EpiParams &e, int i0, int ntile, int lane) {
   const int n = e.n;
   if (i0 >= n) return;
@@ -408,10 +409,10 @@ __device__ __forceinline__ void prefetch_a_pair(const EpiParams &e, int i0, int 
     const int j = ntile * BN + lane + 32 * k;
     if (j >= n) break;
     const size_t c = static_cast<size_t>(j) * n + i0;
-    ptx::prefetch_l2(e.a_hi + c);
-    ptx::prefetch_l2(e.a_hi + c + last);
-    ptx::prefetch_l2(e.a_lo + c);
-    ptx::prefetch_l2(e.a_lo + c + last);
+    ptx::prefetch_l2_keep(e.a_hi + c);
+    ptx::prefetch_l2_keep(e.a_hi + c + last);
+    ptx::prefetch_l2_keep(e.a_lo + c);
+    ptx::prefetch_l2_keep(e.a_lo + c + last);
   }
 }
 
