@@ -390,11 +390,13 @@ __device__ __forceinline__ void store_chunk(const EpiParams &e, int b, int i, in
 // In one-term launches the drain warps wait for the finished-tile buffer for about half of each
 // tile, so for the square-root flow's RK4 stages they form K = (A_hi - P) + A_lo themselves (the
 // same float32 operations as the epilogue would do, so the same bits): the epilogue, which bounds
-// these launches, then reads two fewer arrays per element.  Measured, this pays up to n = 2048;
-// at n = 4096 A's tile no longer stays in L2 from the tile's start to the end of its products,
-// and the drain's latency-bound loads of it lengthen the tile more than the epilogue gains.
+// these launches, then reads two fewer arrays per element.  With a single BF16 term the drain
+// reads the product once per tile and has the next tile's products to do it in; with E4M3 terms
+// it drains every k-block, and measured, forming K there pays up to n = 2048 only (beyond, the
+// drain's latency-bound loads of A lengthen the tile more than the epilogue gains).
 __device__ __forceinline__ bool drain_forms_k(const TcGemmParams &p, const EpiParams &e) {
-  return p.npairs == 1 && e.mode == EPI_STAGE && e.flow == FA_FLOW_SQRT && e.n <= 2048;
+  return p.npairs == 1 && e.mode == EPI_STAGE && e.flow == FA_FLOW_SQRT &&
+         (!p.fp8 || e.n <= 2048);
 }
 
 // L2 prefetch of A's float32 pair over the 32 rows i0.. and the tile's 128 columns (one 32-row
@@ -652,6 +654,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int npairs = p.npairs, ntl = p.ntl;
       const uint32_t idesc = p.idesc;
       constexpr bool fp8 = FP8;
+      // one BF16 term: the main product accumulates over the whole k extent in one TMEM chunk
+      // per tile (its operands' rounding, 2^-9, dwarfs the accumulator's truncation); other
+      // launches drain it every k-block
+      const bool wk = !FP8 && p.npairs == 1;
       const uint64_t desc0 = ptx::sdesc_sw128(ptx::smem_u32(smem));
       uint32_t g = 0, k = 0;
       int mb = 0;
@@ -665,8 +671,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         for (int kb = 0; kb < kblocks; ++kb, ++k) {
+          const bool open = !wk || kb == 0;              // first k-block of a main chunk
+          const bool close = !wk || kb == kblocks - 1;   // its last
           if (!pwait(full + k % NKB, (k / NKB) & 1u, abort_flag, prof, 1) ||
-              !pwait(mbempty + mb, mph ^ 1u, abort_flag, prof, 2)) {
+              (open && !pwait(mbempty + mb, mph ^ 1u, abort_flag, prof, 2))) {
             fail(abort_flag, err);
             ok = false;
             break;
@@ -685,21 +693,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                   // K-step kk starts 32 bytes further into the 128-byte swizzled rows.
-                  const uint32_t acc = (q == 0) ? (kk > 0) : (kb > 0 || q > 1 || kk > 0);
+                  const uint32_t acc = (q == 0) ? (kk > 0 || (wk && kb > 0)) : (kb > 0 || q > 1 || kk > 0);
                   if (fp8)
                     ptx::tc_mma_f8(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
                   else
                     ptx::tc_mma_bf16(q == 0 ? dmain : dcorr, da + 2u * kk, db + 2u * kk, idesc, acc);
                 }
-                if (q == 0) ptx::tc_commit(mbfull + mb);
+                if (q == 0 && close) ptx::tc_commit(mbfull + mb);
               }
             }
             ptx::tc_commit(kbempty + k % NKB);
           }
           __syncwarp();
           g += ntl;
-          mb ^= 1;
-          if (mb == 0) mph ^= 1u;
+          if (close) {
+            mb ^= 1;
+            if (mb == 0) mph ^= 1u;
+          }
         }
         if (!ok) break;
         if (ptx::elect_one()) ptx::tc_commit(cbfull);
@@ -720,10 +730,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int kblocks = tix.kblocks;
       const bool form_k = drain_forms_k(p, *tix.epi);
       if (form_k) prefetch_a_pair(*tix.epi, tix.mt * BM + q * 32, tix.ntile, lane);
+      // main chunks of this tile: one per k-block, or one in all for a single BF16 term
+      const int nchunks = (!FP8 && p.npairs == 1) ? 1 : kblocks;
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
-      for (int kb = 0; kb < kblocks; ++kb) {
+      for (int kb = 0; kb < nchunks; ++kb) {
         if (!pwait(mbfull + mb, mph, abort_flag, prof, 4, 20)) {
           fail(abort_flag, err);
           ok = false;
