@@ -38,8 +38,8 @@ TOL = WORK.mixed_tol      # stopping tolerance of the BF16 forms
 NPAIRS = {"bf16": 1, "bf16x3": 3, "bf16x4": 4, "bf16x6": 6}[DTYPE]
 # DRAM bytes of one fine-sweep GEMM launch of this workload: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of a 16-slice launch of the same kernel
-# (1.111 GB + 0.666 GB), scaled by the slice count (the RK4 state is streamed once per launch).
-TRAFFIC_BYTES_PER_LAUNCH = (1.110930e9 + 0.666435e9) * 64 / 16
+# (1.104 GB + 0.667 GB), scaled by the slice count (the RK4 state is streamed once per launch).
+TRAFFIC_BYTES_PER_LAUNCH = (1.104483e9 + 0.667307e9) * 64 / 16
 CONFIG = {
     "workload": "exp flow dX/dt=AX, X(0)=I, T=1; n=2048 symmetric, lam~U[-4,0], Haar Q; "
                 "N=64 slices, 64 RK4 steps/slice (F), 1 Euler step/slice (G)",
