@@ -322,6 +322,16 @@ const char *fa_plan_tuning(fa_plan_t p);
  * of such a plan fail with FA_ERR_ARG until this has been called. */
 fa_status fa_plan_set_learned(fa_plan_t p, const float *d_params);
 
+/* Opt-in third fallback to Euler (off by default): with enable != 0, fa_parareal_solve on this
+ * learned plan first runs Step 0 and one iteration with Euler G in the solve's own buffers (one
+ * extra fine sweep, counted in report.t_init_ms), then the learned solve; if the learned solve's
+ * first convergence measure exceeds Euler's, the rest of it uses Euler G (report.g_fallback_iter
+ * = 1).  The first measure mixes the coarse trajectory's error into the comparison, so a G that
+ * converges faster can still trip it: on the wide inverse family at n = 64, N = 8 the Taylor-4
+ * step's first measure is 0.4458 against Euler's 0.4444.  FA_ERR_ARG unless the plan has
+ * coarse_kind = FA_COARSE_LEARNED. */
+fa_status fa_plan_set_learned_check(fa_plan_t p, int enable);
+
 /* Coefficients c (device float32 [N][4]) that the plan's last coarse sweep used, per slice. */
 fa_status fa_plan_learned_coefs(fa_plan_t p, float *d_coef);
 

@@ -130,6 +130,7 @@ struct fa_plan_s {
   // learned coarse propagator
   bool learned = false;          // coarse_kind == FA_COARSE_LEARNED
   bool learned_active = false;   // cleared by the fallback to Euler inside a solve
+  bool learned_check = false;    // compare the first iteration with Euler's (opt-in fallback)
   bool params_set = false;
   float *mlp = nullptr;          // network blob
   float *coef = nullptr;         // [N][4] coefficients of the last coarse sweep
@@ -1459,6 +1460,23 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
   int g_fallback_iter = 0;
   FA_CUDA(cudaEventRecord(ev[0], p->stream));
   FA_TRY(fa_plan_set_matrix(p, dA));
+  double dx_euler1 = INFINITY;   // Euler G's first convergence measure (the opt-in guard's bar)
+  if (p->learned && p->learned_check && d.max_iters > 0) {
+    p->learned_active = false;
+    if (dX0) {
+      FA_CUDA(cudaMemcpyAsync(p->U, dX0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    } else {
+      FA_CUDA(fa::launch_identity(p->U, d.n, p->stream));
+    }
+    FA_TRY(coarse_sweep(p, p->U, nullptr, p->U, p->Gold, nullptr, nullptr));
+    FA_TRY(fine_sweep(p, p->U, p->D, p->Gold));
+    FA_TRY(coarse_sweep(p, p->U, p->D, p->U, p->Gnew, p->norms, p->U));
+    FA_CUDA(fa::launch_max_ratio(p->norms, d.N, p->dx, p->err, p->stream));
+    FA_CUDA(cudaMemcpyAsync(&dx_euler1, p->dx, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    p->learned_active = true;
+  }
   if (dX0) {
     FA_CUDA(cudaMemcpyAsync(p->U, dX0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   } else {
@@ -1509,7 +1527,7 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
       converged = true;
       break;
     }
-    if (p->learned_active && k > 0 && dx > prev_dx) {
+    if (p->learned_active && ((k > 0 && dx > prev_dx) || (k == 0 && dx > dx_euler1))) {
       // Fallback: the rest of the solve runs with Euler G; G(U^k_n) is recomputed with it so
       // that the next correction F(U^k_n) - G(U^k_n) uses one propagator.
       p->learned_active = false;
@@ -1622,6 +1640,13 @@ fa_status fa_learned_records(fa_plan_t p, const double *dU, const double *dF, do
   FA_TRY(check_ready(p, true));
   if (!dU || !dF || !d_records) return set_err(FA_ERR_ARG, "null pointer");
   return records(p, dU, dF, nullptr, d_records, d_scratch, scratch_bytes);
+}
+
+fa_status fa_plan_set_learned_check(fa_plan_t p, int enable) {
+  FA_TRY(check_ready(p, false));
+  if (!p->learned) return set_err(FA_ERR_ARG, "the plan's coarse propagator is not the learned one");
+  p->learned_check = enable != 0;
+  return FA_OK;
 }
 
 fa_status fa_plan_set_recorder(fa_plan_t p, double *d_records, int capacity_pairs, void *d_scratch,

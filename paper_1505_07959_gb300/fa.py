@@ -29,6 +29,7 @@ SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_s
            "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
            "fa_batch_solve", "fa_batch_destroy", "fa_plan_set_learned", "fa_plan_learned_coefs",
            "fa_learned_records_scratch", "fa_learned_records", "fa_plan_set_recorder",
+           "fa_plan_set_learned_check",
            "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam",
            "fa_batch_autotune", "fa_batch_tuning", "fa_plan_autotune", "fa_plan_tuning"]
 FA_COARSE_EULER, FA_COARSE_LEARNED = 0, 1
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_learned_records_scratch": [vp, ctypes.POINTER(sz)],
         "fa_learned_records": [vp, dp, dp, dp, dp, sz],
         "fa_plan_set_recorder": [vp, dp, ctypes.c_int, dp, sz],
+        "fa_plan_set_learned_check": [vp, ctypes.c_int],
         "fa_mlp_forward": [dp, ctypes.c_int, dp, ctypes.c_int, dp, vp],
         "fa_mlp_scratch_bytes": [ctypes.c_int, ctypes.POINTER(sz)],
         "fa_mlp_loss_grad": [dp, ctypes.c_int, dp, dp, dp, dp, sz, vp],
@@ -275,6 +277,10 @@ def fa_learned_records(h, dU, dF, d_records, d_scratch, scratch_bytes: int):
                                              _ptr(d_scratch), scratch_bytes))
 
 
+def fa_plan_set_learned_check(h, enable: bool):
+    _check(load_library().fa_plan_set_learned_check(h, 1 if enable else 0))
+
+
 def fa_plan_set_recorder(h, d_records, capacity: int, d_scratch, scratch_bytes: int):
     _check(load_library().fa_plan_set_recorder(h, _ptr(d_records), int(capacity), _ptr(d_scratch),
                                                scratch_bytes))
@@ -403,6 +409,11 @@ class Plan:
         self.params = self.torch.as_tensor(params, dtype=self.torch.float32).cuda().contiguous()
         assert self.params.numel() == FA_MLP_PARAMS
         fa_plan_set_learned(self.handle, self.params)
+
+    def set_learned_check(self, enable=True):
+        """Opt-in fallback: Euler G for the rest of a solve whose first convergence measure
+        exceeds Euler G's (costs one extra fine sweep per solve)."""
+        fa_plan_set_learned_check(self.handle, enable)
 
     def learned_coefs(self):
         c = self.torch.empty((self.N, FA_MLP_COEFS), dtype=self.torch.float32, device="cuda")

@@ -57,6 +57,7 @@ def test_null_plan_is_rejected(lib):
     assert lib.fa_fine_sweep(None, None, None) == 1
     assert lib.fa_parareal_solve(None, None, None, None, None) == 1
     assert lib.fa_plan_destroy(None) == 0
+    assert lib.fa_plan_set_learned_check(None, 1) == 1
 
 
 def test_product_pair_sets_match_header():

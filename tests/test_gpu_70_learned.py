@@ -318,6 +318,42 @@ def test_growing_dx_switches_to_euler_and_still_terminates():
     plan.close()
 
 
+def test_first_iteration_guard_switches_to_euler_when_worse():
+    """The opt-in guard: with c = (0.5, 0, 0, 0) on the exponential flow the first convergence
+    measure (0.75 in the oracle) exceeds Euler G's (0.09), so the solve continues with Euler G
+    from iteration 1 and, by finite termination, N iterations give the sequential fine solution;
+    without the guard nothing falls back.  With the Taylor-4 step (first measure 1.3e-4) the
+    guard does not fire and leaves the solve bitwise unchanged."""
+    cuda_or_fail()
+    n, T, N, J = 64, 1.0, 8, 8
+    sm = inputs.sym_matrix(n, "exp", 3)
+    pe = fa.Plan(n, 1, T, N, J, max_iters=N, tol=0.0)
+    _, repe = pe.solve(dev(sm.A))
+    pe.close()
+    seq = P.sequential_fine(sm.A, 1, T, N, J)
+    for c, fires in (([0.5, 0.0, 0.0, 0.0], True), ([1.0, 1.0, 1.0, 1.0], False)):
+        plan = _learned_plan(n, 1, T, N, J, _const_params(c), max_iters=N, tol=0.0)
+        X0, rep0 = plan.solve(dev(sm.A))
+        plan.set_learned_check(True)
+        X, rep = plan.solve(dev(sm.A))
+        assert rep0["g_fallback_iter"] != 1
+        if fires:
+            assert rep["g_fallback_iter"] == 1, rep
+            assert rep["dx_history"][0] > repe["dx_history"][0]
+            assert P.rel_fro(host(X), seq) < 1e-12
+        else:
+            # (the growing-dx rule may still act at rounding level, the same way in both solves)
+            assert rep["g_fallback_iter"] == rep0["g_fallback_iter"] != 1
+            assert rep["dx_history"][0] < repe["dx_history"][0]
+            assert np.array_equal(host(X), host(X0))
+        plan.close()
+    euler_plan = fa.Plan(n, 1, T, N, J, max_iters=N, tol=0.0)
+    with pytest.raises(fa.FaError) as e:
+        euler_plan.set_learned_check(True)
+    assert e.value.status == 1
+    euler_plan.close()
+
+
 def test_recorder_collects_the_solve_pairs():
     cuda_or_fail()
     n, T, N, J = 56, 1.0, 4, 4
