@@ -14,7 +14,10 @@
 // L_0 R_0^T is accumulated one 64-wide k-block at a time in a fresh TMEM chunk
 // and drained into float32 registers (round-to-nearest adds); the correction
 // products (2^-8 smaller, so their bias is negligible) accumulate in a second
-// TMEM buffer for the whole tile.
+// TMEM buffer for the whole tile.  A single BF16 term is rounded to 2^-9
+// already, far above that bias, so it accumulates the whole k extent in one
+// main chunk per tile and is drained once (E4M3 terms still drain per k-block,
+// where their per-tile scales are applied).
 //
 // Data movement.  Each k-block's operand term tiles (16 KB each) are loaded
 // once by TMA into a 13-slot shared-memory ring and every term pair that uses
@@ -23,7 +26,8 @@
 // Roles (one CTA per SM, 10 warps): warp 0 issues TMA loads; warp 1 issues
 // tcgen05.mma; warps 2-5 drain each main chunk into a float32 running sum in
 // registers (round-to-nearest adds), add the corrections at the end of the
-// tile and store the finished tile into TMEM; warps 6-9 read it from TMEM
+// tile (or, in one-term launches of the square-root flow, form K = A - P;
+// see drain_forms_k) and store the finished tile into TMEM; warps 6-9 read it from TMEM
 // (one row per thread) and run the epilogue against global memory.  The
 // finished-tile buffer is written only at the end of the next tile, so the
 // epilogue of tile t overlaps all of tile t+1's MMAs.  Tiles are scheduled
