@@ -71,7 +71,10 @@ typedef enum { FA_FLOW_INV = 0, FA_FLOW_EXP = 1, FA_FLOW_SQRT = 2 } fa_flow;
  *            x0y0 + x0y1 + x1y0.
  * FA_BF16X4  products x0y0 + x0y1 + x1y0 + x2y0 (left operand to three terms).
  * FA_BF16X6  every product xa yb with a + b <= 2.
- * All BF16 forms accumulate in float32 on the tensor cores (tcgen05).
+ * All BF16 forms accumulate in float32 on the tensor cores (tcgen05); the multi-term forms
+ * drain the main product x0y0 into float32 registers every 64-wide k-block (the accumulator
+ * truncates), FA_BF16 keeps it in the accumulator over the whole k extent (its own rounding,
+ * 2^-9, is far above that truncation: about 4e-6 relative at k = 4096).
  * FA_FP8E4M3 (fine propagator of the square-root flow only) the RK4 stage operands as E4M3 with
  *            one float32 scale per 128 x 128 tile (delayed scaling: 448 / (2 amax) of the same
  *            tile one stage earlier, saturating conversion), float32 accumulation per 128-wide
@@ -207,7 +210,7 @@ fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, doub
  * outputs and cannot own a workspace).  The paper has no counterpart; this is a convenience
  * of the library.  dL, dR, dC: n x n row-major float64 device arrays, 1 <= n <= 1024;
  * dtype one of FA_BF16* (the tensor-core term products of the planned path, float32
- * accumulation with the main product drained per 64-wide k-block).  The BF16 operand terms
+ * accumulation as described for the dtypes above).  The BF16 operand terms
  * live in a fixed array inside the library (about 12 MB per GPU that loads it, held until
  * process exit); no cudaMalloc, cudaFree or allocating library call is made.  The first call
  * on a device looks the array up (cudaGetSymbolAddress) with that device current; make that
