@@ -173,13 +173,134 @@ def test_constant_networks_reproduce_euler_and_taylor_parareal():
     assert all(np.array_equal(a, b) for a, b in zip(r_g.U, r_t1.U))
 
 
+# --- features, Gershgorin bounds, Adam: pins against hand-computed values ------------------------
+
+def test_gershgorin_bounds_of_hand_built_matrices():
+    """Row discs |z - a_ii| <= sum_{j != i} |a_ij|: a symmetric 3 x 3 with discs [1, 7],
+    [-4.5, -1.5], [-1.5, 3.5], and an upper-triangular one whose row discs ([1, 7], [-3.5, -2.5],
+    [1, 1]) differ from its column discs ([4, 4], [-4, -2], [-1.5, 3.5])."""
+    S3 = np.array([[4.0, 1.0, -2.0], [1.0, -3.0, 0.5], [-2.0, 0.5, 1.0]])
+    assert L.gershgorin(S3) == (-4.5, 7.0)
+    U3 = np.array([[4.0, 1.0, -2.0], [0.0, -3.0, 0.5], [0.0, 0.0, 1.0]])
+    assert L.gershgorin(U3) == (-3.5, 7.0)
+    # Gershgorin's theorem: every eigenvalue of a symmetric matrix lies in [lo, hi]
+    A = inputs.sym_matrix(40, "exp", 11).A
+    lo, hi = L.gershgorin(A)
+    w = np.linalg.eigvalsh(A)
+    assert lo <= w.min() and w.max() <= hi
+
+
+def _diag_features(flow, a, x, t_over_T, dT):
+    """The 8 features of diagonal A = diag(a), X = diag(x), written out entry by entry:
+    Gershgorin radii are 0, Hutchinson is exact (z_i^2 = 1), and Fl(X) is diagonal."""
+    n = len(a)
+    if flow == 0:
+        f = [xi * (1.0 - ai) * xi for ai, xi in zip(a, x)]
+    elif flow == 1:
+        f = [ai * xi for ai, xi in zip(a, x)]
+    else:
+        f = [ai - xi * xi for ai, xi in zip(a, x)]
+    return [t_over_T, dT, min(a), max(a), sum(a) / n, sum(x) / n,
+            math.sqrt(sum(v * v for v in f)) / math.sqrt(n),
+            math.sqrt(sum(v * v for v in x)) / math.sqrt(n)]
+
+
+@pytest.mark.parametrize("flow", FLOWS)
+def test_features_on_diagonal_matrices(flow):
+    a = [0.5, 1.0, 2.0, 4.0]
+    x = [1.0, 0.5, 2.0, -1.0]
+    got = L.features(flow, np.diag(a), np.diag(x), 0.375, 0.125, L.probes(4))
+    want = _diag_features(flow, a, x, 0.375, 0.125)
+    assert np.allclose(got, want, rtol=1e-15, atol=1e-15), (got, want)
+
+
+def test_features_fixed_values():
+    """One case fully by hand: inverse flow, a = (0.5, 1, 2, 4), x = (1, 1/2, 2, -1):
+    Fl = diag(x^2 (1 - a)) = (0.5, 0, -4, -3), so ||Fl||_F / 2 = sqrt(25.25) / 2."""
+    got = L.features(0, np.diag([0.5, 1.0, 2.0, 4.0]), np.diag([1.0, 0.5, 2.0, -1.0]), 0.25, 0.5,
+                     L.probes(4))
+    want = [0.25, 0.5, 0.5, 4.0, 7.5 / 4, 2.5 / 4, math.sqrt(25.25) / 2, math.sqrt(6.25) / 2]
+    assert np.allclose(got, want, rtol=1e-15, atol=1e-15)
+
+
+def _adam_params():
+    p = L.init_params(5)
+    for k in p:
+        p[k] = np.asarray(p[k], dtype=np.float64).copy()
+    return p
+
+
+def test_adam_first_step_is_the_sign_step():
+    """Kingma and Ba (2015), Algorithm 1 with bias correction: from m = v = 0 the first step is
+    -lr g / (|g| + eps) element by element (m_hat = g, v_hat = g^2 exactly)."""
+    p0 = _adam_params()
+    rng = np.random.default_rng(7)
+    g = {k: rng.standard_normal(p0[k].shape) * 10.0 ** rng.uniform(-9, 1, p0[k].shape)
+         for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    lr, eps = 1e-2, 1e-8
+    p1 = L.adam({k: v.copy() for k, v in p0.items()}, g, {}, lr=lr, eps=eps)
+    for k in g:
+        want = p0[k] - lr * g[k] / (np.abs(g[k]) + eps)
+        assert np.allclose(p1[k], want, rtol=1e-12, atol=1e-15), k
+    # tiny gradients: the step is lr g / (|g| + eps), far below lr, not lr sign(g)
+    tiny = {k: np.full(p0[k].shape, 1e-8) for k in g}
+    p2 = L.adam({k: v.copy() for k, v in p0.items()}, tiny, {}, lr=lr, eps=eps)
+    assert np.allclose(p0["b3"] - p2["b3"], lr * 0.5, rtol=1e-9)
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so the bias-
+    corrected step is the same every time: after t steps p = p0 - t lr g / (|g| + eps).  Adam is
+    also invariant to a positive rescaling of the gradient when eps = 0."""
+    p0 = _adam_params()
+    g = {k: np.linspace(-2.0, 3.0, p0[k].size).reshape(p0[k].shape) + 0.01
+         for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    st, p = {}, {k: v.copy() for k, v in p0.items()}
+    lr, eps, t = 1e-3, 1e-8, 25
+    for _ in range(t):
+        p = L.adam(p, g, st, lr=lr, b1=0.8, b2=0.95, eps=eps)
+    for k in g:
+        want = p0[k] - t * lr * g[k] / (np.abs(g[k]) + eps)
+        assert np.allclose(p[k], want, rtol=1e-10, atol=1e-13), k
+    # gradient g then -g: m_hat_2 = (b1 - 1) g / (1 + b1), v_hat_2 = g^2, so the second step
+    # moves back by lr (1 - b1) / (1 + b1) g / (|g| + eps)
+    b1 = 0.9
+    st, p = {}, {k: v.copy() for k, v in p0.items()}
+    p = L.adam(p, g, st, lr=lr, b1=b1, eps=eps)
+    p = L.adam(p, {k: -v for k, v in g.items()}, st, lr=lr, b1=b1, eps=eps)
+    for k in g:
+        s = g[k] / (np.abs(g[k]) + eps)
+        want = p0[k] - lr * s + lr * (1 - b1) / (1 + b1) * s
+        assert np.allclose(p[k], want, rtol=1e-10, atol=1e-13), k
+    rng = np.random.default_rng(8)
+    gs = [{k: rng.standard_normal(p0[k].shape) for k in g} for _ in range(6)]
+    pa, pb, sa, sb = dict(p0), dict(p0), {}, {}
+    for gi in gs:
+        pa = L.adam(pa, gi, sa, lr=1e-3, eps=0.0)
+        pb = L.adam(pb, {k: 1000.0 * v for k, v in gi.items()}, sb, lr=1e-3, eps=0.0)
+    for k in g:
+        assert np.allclose(pa[k], pb[k], rtol=1e-12, atol=1e-15), k
+
+
+def test_paper_norm_hand_computed():
+    """Examples 1 and 2 measure errors as max_ij |E_ij| / max_ij |ref_ij|."""
+    E = np.array([[1.0, -3.0], [2.0, 0.0]])
+    ref = np.array([[0.5, 6.0], [-1.0, 2.0]])
+    assert P.paper_norm(E, ref) == 0.5
+    assert P.paper_norm(-E, -ref) == 0.5
+
+
 def _learned_battery() -> bool:
     """A battery of the pins above, run against the (possibly mutated) learned oracle."""
     checks = [test_taylor_terms_match_exact_one_slice_maps, test_pair_record_gives_the_residual_as_a_quadratic,
               test_gelu_and_backprop_against_finite_differences, test_hutchinson_is_exact_on_diagonals_and_unbiased,
               test_splitmix64_matches_the_published_stream, test_bf16_rounding_ties_to_even,
               test_constant_networks_reproduce_euler_and_taylor_parareal,
-              lambda: [test_euler_and_taylor_coefficients(f) for f in FLOWS]]
+              lambda: [test_euler_and_taylor_coefficients(f) for f in FLOWS],
+              test_gershgorin_bounds_of_hand_built_matrices, test_features_fixed_values,
+              lambda: [test_features_on_diagonal_matrices(f) for f in FLOWS],
+              test_adam_first_step_is_the_sign_step, test_adam_constant_gradient_closed_form,
+              test_paper_norm_hand_computed]
     try:
         for c in checks:
             c()
@@ -194,10 +315,14 @@ def test_unmutated_learned_oracle_passes_battery():
 
 @pytest.mark.parametrize("mutation", ["inv_power", "exp_factorial", "sqrt_cauchy", "gelu_grad",
                                       "backprop_transpose", "splitmix_shift", "bf16_truncate",
-                                      "dd_residual"])
+                                      "dd_residual", "gersh_radius_with_diag", "gersh_columns",
+                                      "gersh_swap", "feature_order", "feature_scale_n",
+                                      "adam_no_bias_correction", "adam_eps_in_sqrt",
+                                      "adam_b2_on_m", "paper_norm_fro"])
 def test_planted_mistakes_in_learned_oracle_are_caught(monkeypatch, mutation):
     real_tt, real_gg, real_lg, real_sm = L.taylor_terms, L.gelu_grad, L.loss_and_grad, L.splitmix64
     real_pr = L.pair_record
+    real_gs, real_ft, real_ad, real_pn = L.gershgorin, L.features, L.adam, P.paper_norm
     if mutation == "inv_power":          # X (BX)^j with the powers off by one
         monkeypatch.setattr(L, "taylor_terms", lambda f, A, X, q=4: (
             [X @ np.linalg.matrix_power((np.eye(A.shape[0]) - A) @ X, j) for j in range(q)]
@@ -244,4 +369,44 @@ def test_planted_mistakes_in_learned_oracle_are_caught(monkeypatch, mutation):
             Z = [dT ** (j + 1) * T for j, T in enumerate(real_tt(flow, A, X0, 4))]
             return M, np.array([np.sum(z * X1) for z in Z]), dd
         monkeypatch.setattr(L, "pair_record", pr)
+    elif mutation == "gersh_radius_with_diag":    # radius includes |a_ii|
+        monkeypatch.setattr(L, "gershgorin", lambda A: (
+            float(np.min(np.diag(A) - np.sum(np.abs(A), axis=1))),
+            float(np.max(np.diag(A) + np.sum(np.abs(A), axis=1)))))
+    elif mutation == "gersh_columns":             # column discs instead of row discs
+        monkeypatch.setattr(L, "gershgorin", lambda A: real_gs(np.asarray(A).T))
+    elif mutation == "gersh_swap":                # lower and upper bound swapped
+        monkeypatch.setattr(L, "gershgorin", lambda A: real_gs(A)[::-1])
+    elif mutation == "feature_order":             # tr(A)/n and tr(X)/n swapped
+        def ft(*a, **k):
+            f = real_ft(*a, **k).copy()
+            f[[4, 5]] = f[[5, 4]]
+            return f
+        monkeypatch.setattr(L, "features", ft)
+    elif mutation == "feature_scale_n":           # ||Fl(X)||_F / n instead of / sqrt(n)
+        def ft(flow, A, X, *a, **k):
+            f = real_ft(flow, A, X, *a, **k).copy()
+            f[6] /= math.sqrt(A.shape[0])
+            return f
+        monkeypatch.setattr(L, "features", ft)
+    elif mutation in ("adam_no_bias_correction", "adam_eps_in_sqrt", "adam_b2_on_m"):
+        def ad(p, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+            state["t"] = state.get("t", 0) + 1
+            t = state["t"]
+            for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+                m = state.setdefault("m_" + k, np.zeros_like(p[k]))
+                v = state.setdefault("v_" + k, np.zeros_like(p[k]))
+                bm = b2 if mutation == "adam_b2_on_m" else b1
+                m[:] = bm * m + (1 - bm) * g[k]
+                v[:] = b2 * v + (1 - b2) * g[k] * g[k]
+                if mutation == "adam_no_bias_correction":
+                    p[k] = p[k] - lr * m / (np.sqrt(v) + eps)
+                elif mutation == "adam_eps_in_sqrt":
+                    p[k] = p[k] - lr * (m / (1 - b1 ** t)) / np.sqrt(v / (1 - b2 ** t) + eps)
+                else:
+                    p[k] = p[k] - lr * (m / (1 - bm ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+            return p
+        monkeypatch.setattr(L, "adam", ad)
+    elif mutation == "paper_norm_fro":            # Frobenius instead of max-abs
+        monkeypatch.setattr(P, "paper_norm", lambda E, ref: P.fro(E) / P.fro(ref))
     assert not _learned_battery(), mutation
