@@ -36,6 +36,9 @@ WORK = inputs.EXP_N2048
 DTYPE = WORK.dtype        # split-BF16 products: every term pair x_a y_b with a + b <= 2
 TOL = WORK.mixed_tol      # stopping tolerance of the BF16 forms
 NPAIRS = {"bf16": 1, "bf16x3": 3, "bf16x4": 4, "bf16x6": 6}[DTYPE]
+ACCURACY = 1e-6           # a solve counts only if ||X - exp(A)||_F / ||exp(A)||_F <= this
+FP64_ITERS = 6            # float64 parareal iterations of this workload to tol 1e-10 (the
+                          # eigenvalue-space oracle's count; checked by the CPU test suite)
 # DRAM bytes of one fine-sweep GEMM launch of this workload: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of a 16-slice launch of the same kernel
 # (1.104 GB + 0.667 GB), scaled by the slice count (the RK4 state is streamed once per launch).
@@ -46,6 +49,11 @@ CONFIG = {
     "products": DTYPE + " on tcgen05 (BF16 terms, float32 accumulate, main product drained per k-block)",
     "state": "RK4 state double-float32, parareal correction and norms float64",
     "tol": TOL,
+    "tol_note": "the configuration stops at 1e-10 (written for float64); the BF16x6 fine "
+                "propagator is deterministic but not smooth below ~2^-24 relative, so its "
+                "parareal update stalls near 6e-9 and the mixed form stops at 1e-8 (5 iterations "
+                "where the float64 oracle needs 6 to reach 1e-10); accuracy is gated instead: "
+                "rel. err vs exp(A) <= 1e-6",
     "l2": "working set ~20 GB >> 129 MB L2 (no flush needed)",
     "global_batch": 1,
 }
@@ -58,6 +66,42 @@ def _peaks():
         return float(pk["bf16_tflops_sustained"]), "measured"
     except Exception:
         return 1700.0, "fallback"
+
+
+def fp64_baseline(A, dev, stream):
+    """The plain float64 GPU parareal of the same workload (float64 SIMT products), timed on
+    one fine sweep of one RK4 step per slice (4 stage launches over all slices) and one coarse
+    sweep, extrapolated to a whole solve with the float64 oracle's iteration count to the
+    configuration's tolerance (1e-10)."""
+    import torch
+    from paper_1505_07959_gb300 import fa
+    iters = FP64_ITERS
+    plan = fa.Plan(WORK.n, WORK.flow, WORK.T * 1.0 / WORK.J, WORK.N, fine_steps=1,
+                   coarse_steps=WORK.m, max_iters=1, tol=0.0, fine_dtype="f64", stream=stream)
+    plan.set_matrix(A)
+    U = torch.eye(WORK.n, dtype=torch.float64, device=dev).expand(WORK.N, WORK.n, WORK.n).contiguous()
+    F = torch.empty_like(U)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fa.fa_fine_sweep(plan.handle, U, F)          # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fa.fa_fine_sweep(plan.handle, U, F)
+    e1.record(stream)
+    plan.coarse_sweep(U[0])
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / 1e3           # one RK4 step on all N slices
+    t_coarse = e1.elapsed_time(e2) / 1e3         # (the coarse sweep of dT/J: same cost as dT)
+    plan.close()
+    del U, F
+    solve_s = iters * WORK.J * t_step + (iters + 1) * t_coarse
+    return {"value": 1.0 / solve_s, "unit": UNIT, "dtype": "f64",
+            "iters": iters, "seconds_per_rk4_step_all_slices": t_step,
+            "seconds_per_coarse_sweep": t_coarse,
+            "sample": f"float64 SIMT products on this GPU: one RK4 step on all {WORK.N} slices "
+                      f"(4 stage launches) and one coarse sweep timed with CUDA events, "
+                      f"extrapolated to {iters} iterations x {WORK.J} steps + {iters + 1} coarse "
+                      "sweeps (the float64 oracle's count to tol 1e-10)"}
 
 
 class Clocks:
@@ -270,23 +314,39 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     per_launch_s = e0.elapsed_time(e1) / 1e3 / (sweeps * 4 * WORK.J)
-    flops_per_launch = NPAIRS * 2.0 * WORK.n ** 3 * WORK.N
+    # method work: one n x n x n product per slice per RK4 stage (the exp flow's A Y)
+    flops_per_launch = 2.0 * WORK.n ** 3 * WORK.N
     achieved = flops_per_launch / per_launch_s / 1e12
     peak, peak_kind = _peaks()
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH, "peak_source": f"bf16 sustained, of {peak_kind}",
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+            "peak_source": f"bf16 sustained, of {peak_kind}",
             "kernel": "tc_gemm_kernel (fine sweep, one launch per RK4 stage)",
-            "flops_per_launch": flops_per_launch, "ms_per_launch": per_launch_s * 1e3}
+            "flops_per_launch": flops_per_launch, "ms_per_launch": per_launch_s * 1e3,
+            "work": "method flops: 2 n^3 per slice per RK4 stage",
+            "tensor_pipe": {"term_products": NPAIRS,
+                            "achieved": NPAIRS * achieved,
+                            "frac": NPAIRS * achieved / peak,
+                            "note": f"{DTYPE} runs {NPAIRS} BF16 term products per method "
+                                    "product; this is the tensor pipe's BF16 work rate"}}
     del U, F
+    fp64 = fp64_baseline(A, dev, stream) if not args.no_fp64_baseline else None
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    ok = rel_err <= ACCURACY
+    line = {"metric": METRIC, "value": value if ok else 0.0, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": dict(CONFIG, parallelism=f"{ws} independent problems (one per GPU)"),
-            "rel_err_vs_expm": rel_err, "iters": reps[-1]["iters"], "last_dx": reps[-1]["last_dx"],
+            "rel_err_vs_expm": rel_err, "accuracy_gate": {"bound": ACCURACY, "passed": ok},
+            "iters": reps[-1]["iters"], "last_dx": reps[-1]["last_dx"],
             "phase_ms": {"init": reps[-1]["t_init_ms"], "fine": reps[-1]["t_fine_ms"],
                          "coarse": reps[-1]["t_coarse_ms"]},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+    if not ok:
+        line["e2e"]["value"] = 0.0
+    if fp64 is not None:
+        line["fp64_baseline"] = fp64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample()
     if rank == 0:
@@ -295,6 +355,8 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    if not ok:
+        raise SystemExit(f"accuracy gate failed: rel. err {rel_err:.3e} > {ACCURACY:g}")
 
 
 def main():
@@ -304,6 +366,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -54,3 +54,15 @@ def test_two_gloo_ranks():
         assert t == 2.0 and rate == pytest.approx(ws * 3 / 2.0)   # slowest rank's time
         assert printed == ""
     assert out[0][2] != out[1][2]                                  # independent problems
+
+
+def test_bench_float64_iteration_count_is_the_oracles():
+    """The float64 GPU baseline in the bench line extrapolates with the float64 parareal's
+    iteration count to the workload's tolerance (1e-10); the eigenvalue-space oracle fixes it."""
+    import bench
+    from oracle import scalar as S
+    from paper_1505_07959_gb300 import inputs
+    w = bench.WORK
+    sm = inputs.sym_matrix(w.n, w.kind, w.seed)
+    r = S.parareal(sm.lam, w.flow, w.T, w.N, w.m, w.J, w.K_max, w.tol)
+    assert r.iterations == bench.FP64_ITERS
