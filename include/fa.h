@@ -217,7 +217,10 @@ fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, doub
  * first call before any stream capture.  Calls share the array: calls that overlap on the GPU
  * (other streams, other host threads) race.  FA_ERR_ARG for n outside [1, 1024], a non-BF16
  * dtype or null pointers; FA_ERR_UNSUPPORTED on a device other than sm_103.  Asynchronous on
- * `stream` (a cudaStream_t, NULL = legacy default stream). */
+ * `stream` (a cudaStream_t, NULL = legacy default stream): the status covers the arguments and
+ * the launches only.  A device-side wait of the product kernel that gives up (the bounded waits
+ * that FA_ERR_TIMEOUT reports for planned calls) is not reported by this call; dC is then
+ * partly written. */
 fa_status fa_product_noalloc(int n, int dtype, const double *dL, const double *dR, double *dC,
                              void *stream);
 
@@ -230,6 +233,15 @@ fa_status fa_product_noalloc(int n, int dtype, const double *dL, const double *d
  * [8] epilogue busy, [9] drain busy, [10] kernel cycles per CTA, [11] tiles.
  * NULL switches it off. */
 fa_status fa_debug_set_profile(unsigned long long *d_counters);
+
+/* Diagnostic of the failure detection: later tensor-core launches (process-wide) give up any
+ * device-side wait after `wait_cycles` SM cycles (0 = the default, about 2 s), and, when
+ * skip_loads_cta >= 0, that CTA of each launch issues no operand loads, so its waits run out:
+ * the kernel raises its abort flag, records FA_ERR_TIMEOUT in the plan's error word (reported
+ * by the next synchronising call), waits briefly, releases its tensor memory and returns; no
+ * copy is left in flight.  The other CTAs finish their tiles, so the output is partly written.
+ * (0, -1) restores normal operation.  FA_ERR_ARG for wait_cycles < 0. */
+fa_status fa_debug_set_wait_fault(long long wait_cycles, int skip_loads_cta);
 
 /* ---- Batches: many independent problems of mixed order and flow -------------------------
  *
@@ -249,9 +261,12 @@ fa_status fa_batch_plan(fa_batch_t *out, int count, const int *ns, const int *fl
                         size_t *workspace_bytes);
 fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_workspace, size_t bytes);
 /* dA[i] / dXout[i]: device pointers (host array of `count`), row-major float64 n_i x n_i.
+ * A problem that meets tol leaves the batch: dXout[i] receives its U_N of that iteration, and
+ * later launches no longer contain its tiles (the segment tables are rebuilt and the iteration
+ * graph captured again), so each problem runs exactly the iterations a single solve of it runs.
  * iters[i] (host, optional): iteration at which problem i met tol (or the count run);
- * last_dx[i] (host, optional): its last convergence measure.  Returns FA_ERR_NOT_CONVERGED
- * (outputs written) if some problem missed tol. */
+ * last_dx[i] (host, optional): its convergence measure at that iteration.  Returns
+ * FA_ERR_NOT_CONVERGED (outputs written) if some problem missed tol. */
 fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *dXout, int *iters,
                          double *last_dx);
 fa_status fa_batch_destroy(fa_batch_t b);

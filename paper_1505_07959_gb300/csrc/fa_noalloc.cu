@@ -61,8 +61,9 @@ extern "C" fa_status fa_product_noalloc(int n, int dtype, const double *dL, cons
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return fa::record_error(FA_ERR_CUDA, cudaGetErrorString(ce));
   int major = 0, minor = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  ce = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (ce != cudaSuccess) return fa::record_error(FA_ERR_CUDA, cudaGetErrorString(ce));
   if (major != 10 || minor != 3)
     return fa::record_error(FA_ERR_UNSUPPORTED, "fa_product_noalloc: device is not sm_103");
   void *scratch = nullptr;

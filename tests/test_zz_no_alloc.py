@@ -28,6 +28,27 @@ def test_no_alloc_product_matches_planned_product_on_two_calls():
         assert np.linalg.norm(out - L @ R) / scale < PRODUCT_TOL[dtype], call
 
 
+@pytest.mark.parametrize("n", [197, 1024])
+def test_no_alloc_product_padded_rows_and_the_array_limit(n):
+    """n = 197 pads each operand row to 200 elements (ldp > n); n = 1024 fills the array."""
+    cuda_or_fail()
+    stream = torch.cuda.current_stream().cuda_stream
+    dtype = "bf16x6"
+    rng = np.random.default_rng(300 + n)
+    L, R = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    plan = fa.Plan(n, fa.FA_FLOW_SQRT, 1.0, 1, fine_steps=1, fine_dtype=dtype)
+    ref = host(plan.debug_product(dev(L), dev(R)))
+    plan.close()
+    scale = np.linalg.norm(L) * np.linalg.norm(R)
+    for call in range(2):
+        C = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        fa.fa_product_noalloc(n, fa.DTYPES[dtype], dev(L), dev(R), C, stream)
+        out = host(C)
+        assert np.all(np.isfinite(out)), call
+        assert np.linalg.norm(out - ref) / scale < PRODUCT_TOL[dtype], call
+        assert np.linalg.norm(out - L @ R) / scale < PRODUCT_TOL[dtype], call
+
+
 def test_no_alloc_rejects_sizes_beyond_its_array():
     cuda_or_fail()
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
