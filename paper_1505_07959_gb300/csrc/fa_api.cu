@@ -20,6 +20,8 @@ namespace {
 
 thread_local std::string g_last_error;
 unsigned long long *g_prof = nullptr;   // diagnostics: per-role cycle counters of the TC kernel
+long long g_wait_cycles = 0;            // diagnostics: wait limit of TC launches (0 = default)
+int g_skip_loads_cta = -1;              // diagnostics: CTA that issues no loads (-1 = none)
 thread_local unsigned long long g_launches = 0;
 
 fa_status set_err(fa_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
@@ -300,6 +302,8 @@ TcGemmParams tc_launch_params(int n, int nb, int l_batched, int r_batched, const
   g.kblocks = (n + 63) / 64;
   tc_schedule(ps, g);
   g.prof = g_prof;
+  g.wait_cycles = g_wait_cycles;
+  g.skip_loads_cta = g_skip_loads_cta;
   g.prefetch_state = ps.npairs == 1 ? 1 : 0;   // measured: +10 % at one pair, -2 % at six
   g.idesc = ptx::idesc_bf16_f32(TC_BM, TC_BN);
   return g;
@@ -1603,6 +1607,13 @@ fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, doub
     return tc(p, p->tmVl[0], p->tmVr[0], tc_params(p, 1, 0, 0, e));
   }
   return f64(p, dL, 0, dR, 0, 1, e);
+}
+
+fa_status fa_debug_set_wait_fault(long long wait_cycles, int skip_loads_cta) {
+  if (wait_cycles < 0) return set_err(FA_ERR_ARG, "wait_cycles must be >= 0");
+  g_wait_cycles = wait_cycles;
+  g_skip_loads_cta = skip_loads_cta < 0 ? -1 : skip_loads_cta;
+  return FA_OK;
 }
 
 fa_status fa_debug_set_profile(unsigned long long *d_counters) {

@@ -130,6 +130,9 @@ struct TcGemmParams {
                               // one term pair; with six it competes with the operand feed)
   const TcSegment *segs;      // ragged launch: per-problem segments (device), else null
   int nseg;
+  long long wait_cycles;      // limit of every mbarrier wait (<= 0: ptx::kWaitCycles)
+  int skip_loads_cta;         // diagnostics: this CTA issues no operand loads (-1: none), so
+                              // its waits run out and the launch reports FA_ERR_TIMEOUT
   EpiParams epi;
 };
 

@@ -11,7 +11,8 @@ namespace fa {
 namespace ptx {
 
 // A wait on an mbarrier gives up after this many SM cycles (about 2 s at
-// 2 GHz); legitimate waits in these kernels last microseconds.
+// 2 GHz) unless a launch sets its own limit; legitimate waits in these kernels
+// last microseconds.
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -50,16 +51,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity to complete.  Returns
-// false if the CTA's abort flag is raised or the cycle limit is exceeded.
+// false if the CTA's abort flag is raised or `limit` cycles have passed.
 // With sleep_ns > 0 the waiting warp backs off between polls, leaving issue
 // slots to the warps that share its scheduler.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
-                                          unsigned sleep_ns = 0) {
+                                          long long limit, unsigned sleep_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
     if (sleep_ns) __nanosleep(sleep_ns);
   }
   return true;

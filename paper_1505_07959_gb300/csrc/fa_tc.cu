@@ -527,10 +527,11 @@ __device__ __forceinline__ TileInfo tile_info(const TcGemmParams &p, const CUten
 
 // Bounded wait that, when `prof` is set, adds the cycles spent waiting to prof[slot].
 __device__ __forceinline__ bool pwait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                      unsigned long long *prof, int slot, unsigned sleep_ns = 0) {
-  if (!prof) return ptx::mbar_wait(bar, parity, abort_flag, sleep_ns);
+                                      long long limit, unsigned long long *prof, int slot,
+                                      unsigned sleep_ns = 0) {
+  if (!prof) return ptx::mbar_wait(bar, parity, abort_flag, limit, sleep_ns);
   const long long t0 = clock64();
-  const bool ok = ptx::mbar_wait(bar, parity, abort_flag, sleep_ns);
+  const bool ok = ptx::mbar_wait(bar, parity, abort_flag, limit, sleep_ns);
   atomicAdd(prof + slot, static_cast<unsigned long long>(clock64() - t0));
   return ok;
 }
@@ -594,6 +595,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   const long long t_kernel0 = clock64();
   int *const err = p.epi.err;
+  const long long wl = p.wait_cycles > 0 ? p.wait_cycles : ptx::kWaitCycles;
 
   if (warp == 0) {
     // ---------------- TMA producer: each k-block's term tiles, once ----------------
@@ -601,7 +603,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // over the launch) signals barrier full[k % NKB] (phase k / NKB) once all its tiles
     // have landed.  Before refilling a slot the producer waits until the k-block that last
     // used it, (g - NSLOT) / ntl, has been consumed (kbempty, same indexing).
-    if (lane == 0) {
+    // (diagnostics: a CTA told to issue no loads leaves its waits to run out)
+    if (lane == 0 && p.skip_loads_cta != static_cast<int>(blockIdx.x)) {
       int side[6], term[6];
 #pragma unroll
       for (int t = 0; t < 6; ++t) {
@@ -623,7 +626,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t gt = g + ti;
             if (gt >= static_cast<uint32_t>(NSLOT)) {
               const uint32_t kp = (gt - NSLOT) / ntl;
-              if (!pwait(kbempty + kp % NKB, (kp / NKB) & 1u, abort_flag, p.prof, 0)) {
+              if (!pwait(kbempty + kp % NKB, (kp / NKB) & 1u, abort_flag, wl, p.prof, 0)) {
                 fail(abort_flag, err);
                 ok = false;
                 continue;
@@ -670,15 +673,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       unsigned long long *prof = lane == 0 ? p.prof : nullptr;
       for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
         const int kblocks = tile_info(p, &tmL, &tmR, tile).kblocks;
-        if (!pwait(cbempty, cph ^ 1u, abort_flag, prof, 3)) {
+        if (!pwait(cbempty, cph ^ 1u, abort_flag, wl, prof, 3)) {
           fail(abort_flag, err);
           break;
         }
         for (int kb = 0; kb < kblocks; ++kb, ++k) {
           const bool open = !wk || kb == 0;              // first k-block of a main chunk
           const bool close = !wk || kb == kblocks - 1;   // its last
-          if (!pwait(full + k % NKB, (k / NKB) & 1u, abort_flag, prof, 1) ||
-              (open && !pwait(mbempty + mb, mph ^ 1u, abort_flag, prof, 2))) {
+          if (!pwait(full + k % NKB, (k / NKB) & 1u, abort_flag, wl, prof, 1) ||
+              (open && !pwait(mbempty + mb, mph ^ 1u, abort_flag, wl, prof, 2))) {
             fail(abort_flag, err);
             ok = false;
             break;
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
       for (int kb = 0; kb < nchunks; ++kb) {
-        if (!pwait(mbfull + mb, mph, abort_flag, prof, 4, 20)) {
+        if (!pwait(mbfull + mb, mph, abort_flag, wl, prof, 4, 20)) {
           fail(abort_flag, err);
           ok = false;
           break;
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (mb == 0) mph ^= 1u;
       }
       if (!ok) break;
-      if (!pwait(cbfull, cph, abort_flag, prof, 5, 20)) {
+      if (!pwait(cbfull, cph, abort_flag, wl, prof, 5, 20)) {
         fail(abort_flag, err);
         break;
       }
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         ptx::tmem_wait_st();
       }
-      if (!pwait(finempty, fph ^ 1u, abort_flag, prof, 6, 100)) {
+      if (!pwait(finempty, fph ^ 1u, abort_flag, wl, prof, 6, 100)) {
         fail(abort_flag, err);
         break;
       }
@@ -867,7 +870,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int i = mt * BM + row;
       const bool kform = drain_forms_k(p, e);   // the finished tile holds K, not the product
       if (ti_.prefetch) prefetch_tile_state(e, gb, mt, ntile, q, lane, kform);
-      if (!pwait(finfull, fph, abort_flag, prof, 7, 100)) {
+      if (!pwait(finfull, fph, abort_flag, wl, prof, 7, 100)) {
         fail(abort_flag, err);
         break;
       }

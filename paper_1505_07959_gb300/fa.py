@@ -25,7 +25,7 @@ DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16
           "bf16x6": FA_BF16X6, "fp8e4m3": FA_FP8E4M3}
 SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_sweep",
            "fa_coarse_sweep", "fa_refine", "fa_parareal_solve", "fa_parareal_solve_host",
-           "fa_debug_product", "fa_debug_set_profile", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
+           "fa_debug_product", "fa_debug_set_profile", "fa_debug_set_wait_fault", "fa_product_noalloc", "fa_plan_destroy", "fa_status_string", "fa_last_error",
            "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
            "fa_batch_solve", "fa_batch_destroy", "fa_plan_set_learned", "fa_plan_learned_coefs",
            "fa_learned_records_scratch", "fa_learned_records", "fa_plan_set_recorder",
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fa_parareal_solve_host": [vp, dp, dp, dp, ctypes.POINTER(fa_report)],
         "fa_debug_product": [vp, dp, dp, dp],
         "fa_debug_set_profile": [dp],
+        "fa_debug_set_wait_fault": [ctypes.c_longlong, ctypes.c_int],
         "fa_product_noalloc": [ctypes.c_int, ctypes.c_int, dp, dp, dp, vp],
         "fa_plan_destroy": [vp],
         "fa_batch_plan": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -188,6 +189,10 @@ def fa_debug_product(h, dL, dR, dC):
 
 def fa_debug_set_profile(d_counters):
     _check(load_library().fa_debug_set_profile(_ptr(d_counters)))
+
+
+def fa_debug_set_wait_fault(wait_cycles: int, skip_loads_cta: int):
+    _check(load_library().fa_debug_set_wait_fault(wait_cycles, skip_loads_cta))
 
 
 def fa_product_noalloc(n: int, dtype: int, dL, dR, dC, stream_handle: int):

@@ -109,3 +109,8 @@ def test_blob_and_record_sizes_match_header():
     assert re.search(r"#define FA_PROBE_SEED 0x150507959ULL", src)
     assert fa.FA_PROBE_SEED == L.PROBE_SEED
     assert L.to_blob(L.init_params(0)).size == fa.FA_MLP_PARAMS
+
+
+def test_wait_fault_switch_checks_its_argument(lib):
+    assert lib.fa_debug_set_wait_fault(-1, 0) == 1          # FA_ERR_ARG
+    assert lib.fa_debug_set_wait_fault(0, -1) == 0          # normal operation
