@@ -1074,6 +1074,10 @@ struct fa_batch_s {
   int prefetch_b[kBuckets] = {0, 0, 0, 0, 0, 0}, raster_b[kBuckets] = {0, 0, 0, 0, 0, 0};
   int order = 0;                         // 0: problems as given, 1: largest n first
   std::string tuning;
+  // problems still iterating in the current solve (empty = all): a problem that met the
+  // tolerance leaves the segment tables, so later launches skip its tiles
+  std::vector<char> active;
+  bool is_active(int i) const { return active.empty() || active[i]; }
   ~fa_batch_s() {
     for (auto *p : plans) delete p;
     if (graph) cudaGraphExecDestroy(graph);
@@ -1140,6 +1144,7 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
       t = fa_batch_s::Table();
       t.first = host.size();
       for (int idx : ord) {
+        if (!b->is_active(idx)) continue;
         fa_plan_s *p = b->plans[idx];
         const fa_problem_desc &d = p->d;
         const int bk = size_bucket(d.n);
@@ -1193,6 +1198,7 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
           fa_batch_s::Table &t = b->coarse[b->coarse_index(mode, n, sub, phase)];
           t.first = host.size();
           for (int idx : ord) {
+            if (!b->is_active(idx)) continue;
             fa_plan_s *p = b->plans[idx];
             const fa_problem_desc &d = p->d;
             const int m = d.coarse_steps;
@@ -1260,6 +1266,13 @@ fa_status upload_tables(fa_batch_s *b) {
   return FA_OK;
 }
 
+// Every problem back in the segment tables (the start of a solve, and the autotuner).
+fa_status activate_all(fa_batch_s *b) {
+  if (b->active.empty()) return FA_OK;
+  b->active.clear();
+  return upload_tables(b);
+}
+
 fa_status launch_table(fa_batch_s *b, const fa_batch_s::Table &t) {
   if (t.nseg == 0) return FA_OK;
   TcGemmParams g = fa::tc_launch_params(128, 1, 0, 0, b->plans[0]->ps);
@@ -1270,7 +1283,9 @@ fa_status launch_table(fa_batch_s *b, const fa_batch_s::Table &t) {
 }
 
 fa_status batch_coarse(fa_batch_s *b, int mode) {
-  for (fa_plan_s *p : b->plans) {
+  for (int i = 0; i < b->count; ++i) {
+    if (!b->is_active(i)) continue;
+    fa_plan_s *p = b->plans[i];
     FA_CUDA(fa::launch_split_terms(p->U, 1, p->d.n, p->ldp, p->Vl[0],
                                    p->needs_l() ? p->ps.terms_l : 0, p->strideV, p->Vr[0],
                                    p->ps.terms_r, p->strideV, 0, b->stream));
@@ -1283,7 +1298,9 @@ fa_status batch_coarse(fa_batch_s *b, int mode) {
 }
 
 fa_status batch_iteration(fa_batch_s *b) {
-  for (fa_plan_s *p : b->plans) {
+  for (int i = 0; i < b->count; ++i) {
+    if (!b->is_active(i)) continue;
+    fa_plan_s *p = b->plans[i];
     FA_CUDA(fa::launch_load_state(p->U, b->N, p->d.n, p->ldp, p->x_hi, p->x_lo, p->Yl[0],
                                   p->needs_l() ? p->ps.terms_l : 0, p->strideY, p->Yr[0],
                                   p->ps.terms_r, p->strideY, b->stream));
@@ -1811,6 +1828,7 @@ fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_ws, size_t bytes) {
     b->raster_b[k] = 0;
   }
   b->order = 0;
+  b->active.clear();
   FA_TRY(upload_tables(b));
   std::vector<fa::BatchNorm> norms(b->count);
   for (int i = 0; i < b->count; ++i) {
@@ -1895,6 +1913,7 @@ fa_status fa_batch_autotune(fa_batch_t b, const double *const *dA, const char *c
   if (!b) return set_err(FA_ERR_ARG, "null batch");
   if (!b->ws) return set_err(FA_ERR_WORKSPACE, "no workspace bound");
   if (!dA) return set_err(FA_ERR_ARG, "null pointer");
+  FA_TRY(activate_all(b));
   char key[160];
   snprintf(key, sizeof(key), "fa-batch count=%d N=%d J=%d dtype=%d sig=%016llx", b->count, b->N,
            b->J, b->dtype, batch_signature(b));
@@ -2073,6 +2092,7 @@ fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *d
   if (!b) return set_err(FA_ERR_ARG, "null batch");
   if (!b->ws) return set_err(FA_ERR_WORKSPACE, "no workspace bound");
   if (!dA || !dXout) return set_err(FA_ERR_ARG, "null pointer");
+  FA_TRY(activate_all(b));
   FA_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
   for (int i = 0; i < b->count; ++i) {
     fa_plan_s *p = b->plans[i];
@@ -2082,7 +2102,7 @@ fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *d
     FA_CUDA(fa::launch_identity(p->U, p->d.n, b->stream));
   }
   FA_TRY(batch_coarse(b, 0));       // Step 0 (eq. eqStep0) for every problem
-  std::vector<double> dx(b->count, INFINITY);
+  std::vector<double> dx(b->count, INFINITY), dx_at(b->count, INFINITY);
   std::vector<int> conv_at(b->count, 0);
   int done = 0, k = 0;
   for (; k < b->max_iters && done < b->count; ++k) {
@@ -2116,19 +2136,30 @@ fa_status fa_batch_solve(fa_batch_t b, const double *const *dA, double *const *d
     FA_CUDA(cudaMemcpyAsync(dx.data(), b->d_dx, b->count * sizeof(double), cudaMemcpyDeviceToHost,
                             b->stream));
     FA_CUDA(cudaStreamSynchronize(b->stream));
+    bool changed = false;
     for (int i = 0; i < b->count; ++i) {
       if (!conv_at[i] && dx[i] < b->tol) {
+        // converged: its result is U_N of this iteration, and it leaves the later launches
         conv_at[i] = k + 1;
+        dx_at[i] = dx[i];
         ++done;
+        fa_plan_s *p = b->plans[i];
+        FA_CUDA(cudaMemcpyAsync(dXout[i], p->U + static_cast<size_t>(b->N) * p->nn,
+                                p->nn * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+        if (b->active.empty()) b->active.assign(b->count, 1);
+        b->active[i] = 0;
+        changed = true;
       }
     }
+    if (changed && done < b->count && k + 1 < b->max_iters) FA_TRY(upload_tables(b));
   }
   for (int i = 0; i < b->count; ++i) {
     fa_plan_s *p = b->plans[i];
-    FA_CUDA(cudaMemcpyAsync(dXout[i], p->U + static_cast<size_t>(b->N) * p->nn,
-                            p->nn * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    if (!conv_at[i])
+      FA_CUDA(cudaMemcpyAsync(dXout[i], p->U + static_cast<size_t>(b->N) * p->nn,
+                              p->nn * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     if (iters) iters[i] = conv_at[i] ? conv_at[i] : k;
-    if (last_dx) last_dx[i] = dx[i];
+    if (last_dx) last_dx[i] = conv_at[i] ? dx_at[i] : dx[i];
   }
   int h = 0;
   FA_CUDA(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));

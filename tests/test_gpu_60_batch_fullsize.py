@@ -31,11 +31,11 @@ def test_mixed_batch_of_512_problems():
     print(f"512-problem batch: {dt * 1e3:.0f} ms, {512 / dt:.1f} solves/s, "
           f"iterations run {max(iters)}, per-problem {np.bincount(iters)}")
     assert st == fa.FA_OK
-    kmax = max(iters)
     rng = np.random.default_rng(0)
     for i in sorted(rng.choice(512, 24, replace=False)):
         w, sm = probs[i]
-        ref = S.to_matrix(sm.Q, S.parareal(sm.lam, w.flow, w.T, N, w.m, J, kmax, 0.0).u[N])
+        # a problem leaves the batch once it converged: its result is its iterate then
+        ref = S.to_matrix(sm.Q, S.parareal(sm.lam, w.flow, w.T, N, w.m, J, iters[i], 0.0).u[N])
         e = rel(host(Xs[i]), ref)
         assert e < 1e-6, (i, w.n, w.flow, e)
     b.close()
