@@ -31,6 +31,9 @@ def test_tiny_inverse_workload_f64():
     assert rep["iters"] == ref.iterations
     assert rel(X, ref.U[w.N]) < 1e-12
     assert rel(X, closed.inv_lu(sm.A)) < 1e-10
+    # the paper's own error measure (Section 2, Example 1): max_ij |E_ij| / max_ij |A_ij|
+    assert orc.paper_norm(X - ref.U[w.N], sm.A) < 1e-12
+    assert orc.paper_norm(X - closed.inv_lu(sm.A), sm.A) < 1e-10
     for a, b in zip(rep["dx_history"], ref.dx_history):
         assert abs(a - b) <= 1e-8 * b + 1e-15
 

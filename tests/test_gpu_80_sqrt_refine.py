@@ -81,3 +81,25 @@ def test_exp_flow_has_no_refinement():
         plan.refine(dev(np.eye(32)))
     assert e.value.status == 7
     plan.close()
+
+
+def test_refinement_at_the_square_root_workloads_order():
+    """n = 4096 (the square-root workload: lam log-U[1e-3, 1], the flow state at T = 20 from
+    X(0) = I, plus BF16-level symmetric noise): one Newton step against the oracle's exact-
+    Sylvester Newton step, and four steps against A^{1/2}."""
+    cuda_or_fail()
+    n = 4096
+    sm, X0 = _flow_state(n, 0, 1e-3)
+    exact = S.to_matrix(sm.Q, np.sqrt(sm.lam))
+    for steps in (1, 4):
+        plan = fa.Plan(n, fa.FA_FLOW_SQRT, 20.0, 1, 1, coarse_steps=2, fine_dtype="bf16",
+                       refine_steps=steps)
+        plan.set_matrix(dev(sm.A))
+        got = host(plan.refine(dev(X0)))
+        plan.close()
+        assert np.array_equal(got, got.T)
+        if steps == 1:
+            want = RF.newton_sylvester_sqrt(sm.A, X0, 1)
+            assert P.rel_fro(got, want) <= 1e-6, P.rel_fro(got, want)
+        else:
+            assert P.rel_fro(got, exact) < 1e-10, P.rel_fro(got, exact)

@@ -1,7 +1,7 @@
-"""Host logic of the product-accuracy command: the BF16 rounding of its exact reference."""
+"""Host logic of the product-accuracy test: the BF16 rounding of its exact reference."""
 import numpy as np
 
-from paper_1505_07959_gb300.product_case import bf16_rn, bias, rel
+from product_accuracy import bf16_rn, bias, rel
 
 
 def test_bf16_rn_is_nearest_with_eight_significant_bits():
