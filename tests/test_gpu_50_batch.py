@@ -58,7 +58,7 @@ def test_batch_stops_per_problem_at_tolerance_and_repeats_bitwise():
     for i, (n, f, T, m, sm) in enumerate(zip(ns, flows, Ts, ms, mats)):
         solo = orc.parareal(sm.A, f, T, N, m, J, N, 1e-7)
         assert abs(it1[i] - solo.iterations) <= 1, (i, it1[i], solo.iterations)
-        assert dx1[i] < 1e-7
+        assert dx1[i] < 1e-7 or it1[i] == N     # converged, or ran every iteration
         # a converged problem leaves the batch: its result is its iterate at convergence
         ref = orc.parareal(sm.A, f, T, N, m, J, it1[i], 0.0)
         assert rel(host(X1[i]), ref.U[N]) < 1e-6
