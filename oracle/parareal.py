@@ -70,6 +70,32 @@ def rk4(flow: int, X: np.ndarray, A: np.ndarray, dT: float, J: int) -> np.ndarra
     return X
 
 
+def crank_nicolson(flow: int, X: np.ndarray, A: np.ndarray, dT: float, J: int) -> np.ndarray:
+    """J Crank-Nicolson steps of size h = dT/J for the linear flow dX/dt = A X (the propagator
+    of Section 2, Example 2): (I - h/2 A) X_{j+1} = (I + h/2 A) X_j, solved by LU per step."""
+    if flow != FLOW_EXP:
+        raise ValueError("Crank-Nicolson is used for the linear (exponential) flow")
+    n = A.shape[0]
+    h = dT / J
+    Lm = np.eye(n) - (h / 2) * A
+    Rm = np.eye(n) + (h / 2) * A
+    for _ in range(J):
+        X = np.linalg.solve(Lm, Rm @ X)
+    return X
+
+
+def propagator(scheme: str, flow: int, A: np.ndarray, dT: float, steps: int):
+    """The one-slice map of a scheme: "rk4" (classical RK4), "euler" (explicit Euler, Example
+    1's propagators) or "cn" (Crank-Nicolson, Example 2's), `steps` steps per slice."""
+    if scheme == "rk4":
+        return lambda x: rk4(flow, x, A, dT, steps)
+    if scheme == "euler":
+        return lambda x: euler(flow, x, A, dT, steps)
+    if scheme == "cn":
+        return lambda x: crank_nicolson(flow, x, A, dT, steps)
+    raise ValueError(scheme)
+
+
 def fro(X: np.ndarray) -> float:
     """Frobenius norm ||X||_F = tr(X^T X)^{1/2} (Section 3's <.,.>_F norm)."""
     return float(np.sqrt(np.sum(X * X)))
@@ -130,8 +156,10 @@ def parareal_generic(X0: np.ndarray, N: int,
 
 def parareal(A: np.ndarray, flow: int, T: float, N: int, m: int, J: int, K_max: int,
              tol: float, X0: Optional[np.ndarray] = None, keep_all: bool = False,
-             coarse: str = "euler") -> PararealResult:
-    """Parareal for one matrix flow: Euler G (m substeps), RK4 F (J steps) per slice.
+             coarse: str = "euler", fine: str = "rk4") -> PararealResult:
+    """Parareal for one matrix flow: G = m steps of the coarse scheme (forward Euler, or
+    Crank-Nicolson with coarse="cn"), F = J steps of the fine scheme ("rk4", "euler" or "cn")
+    per slice.
 
     coarse="fine" replaces G by F (a special case in which the correction makes
     every slice exact after one iteration).
@@ -141,13 +169,16 @@ def parareal(A: np.ndarray, flow: int, T: float, N: int, m: int, J: int, K_max: 
     if X0 is None:
         X0 = np.eye(n)
     dT = T / N
+    f_map = propagator(fine, flow, A, dT, J)
 
     def F(_n, x):
-        return rk4(flow, x, A, dT, J)
+        return f_map(x)
 
-    if coarse == "euler":
+    if coarse in ("euler", "cn"):
+        g_map = propagator(coarse, flow, A, dT, m)
+
         def G(_n, x):
-            return euler(flow, x, A, dT, m)
+            return g_map(x)
     elif coarse == "fine":
         G = F
     else:
@@ -156,14 +187,15 @@ def parareal(A: np.ndarray, flow: int, T: float, N: int, m: int, J: int, K_max: 
 
 
 def sequential_fine(A: np.ndarray, flow: int, T: float, N: int, J: int,
-                    X0: Optional[np.ndarray] = None, all_slices: bool = False):
-    """The sequential fine solution: F applied N times from X0 (N*J RK4 steps)."""
+                    X0: Optional[np.ndarray] = None, all_slices: bool = False, fine: str = "rk4"):
+    """The sequential fine solution: F applied N times from X0 (N*J steps of the scheme)."""
     A = np.asarray(A, dtype=np.float64)
     X = np.eye(A.shape[0]) if X0 is None else np.asarray(X0, dtype=np.float64)
     dT = T / N
+    f_map = propagator(fine, flow, A, dT, J)
     out = [X]
     for _ in range(N):
-        X = rk4(flow, X, A, dT, J)
+        X = f_map(X)
         out.append(X)
     return out if all_slices else X
 

@@ -115,6 +115,39 @@ INV_N1024_WIDE = Workload("inverse flow, n=1024, lam~logU[1e-2,1], N=64, J=64", 
                           1024, "inv_wide", 1.0, 64, 1, 64, 64, 1e-8)
 
 
+def paper_example_matrix(example: int, n: int = 80) -> np.ndarray:
+    """The matrices of the paper's Section 2 examples, from the 1-D Laplacian L (order 80, scaled
+    by 1/h^2, h = 1/81: the reading under which the examples' explicit propagators resolve the
+    spectrum): Example 1 inverts L / 2^10, Example 2 exponentiates B = -L / 2^10."""
+    a = laplacian_1d(n, scaled=True) / 2.0 ** 10
+    if example == 1:
+        return a
+    if example == 2:
+        return -a
+    raise ValueError(example)
+
+
+@dataclasses.dataclass
+class PaperExample:
+    """The paper's own parareal setups (Section 2): N slices of [0, 1], J fine steps per slice,
+    the schemes of F and G, one coarse step per slice."""
+
+    name: str
+    flow: int
+    example: int
+    N: int = 25
+    J: int = 200
+    fine: str = "euler"
+    coarse: str = "euler"
+    T: float = 1.0
+
+
+PAPER_EX1 = PaperExample("Example 1: inverse of L/2^10 (n=80), explicit Euler G and F, N=25, J=200",
+                         FLOW_INV, 1)
+PAPER_EX2 = PaperExample("Example 2: exp(-L/2^10) (n=80), Crank-Nicolson G and F, N=25, J=200",
+                         FLOW_EXP, 2, fine="cn", coarse="cn")
+
+
 def batched_problems(count: int = 512, n_lo: int = 32, n_hi: int = 512, base_seed: int = 0):
     """Mixed batch: n log-uniform in [n_lo, n_hi], flows cycling inv/exp/sqrt.
 

@@ -376,3 +376,50 @@ def test_newton_sign_sqrt_matches_eigen_newton():
     Xa = RF.newton_sylvester_sqrt(sm.A, X0, 4)
     Xb = RF.newton_sign_sqrt(sm.A, X0, 4, 18)
     assert P.rel_fro(Xa, exact) < 1e-10 and P.rel_fro(Xb, exact) < 1e-10
+
+
+# --- the paper's own propagators: explicit Euler F and Crank-Nicolson (Section 2) ------------
+
+
+def test_crank_nicolson_is_the_cayley_step_per_eigenvalue():
+    """On a symmetric A every CN step multiplies eigencomponent i by (1 + h l_i / 2) /
+    (1 - h l_i / 2), so J steps from I give Q diag(r_i^J) Q^T; the scheme is second order."""
+    sm = inputs.sym_matrix(12, "exp", 21)
+    dT, J = 0.25, 5
+    h = dT / J
+    X = P.crank_nicolson(P.FLOW_EXP, np.eye(12), sm.A, dT, J)
+    r = (1 + h * sm.lam / 2) / (1 - h * sm.lam / 2)
+    assert P.rel_fro(X, S.to_matrix(sm.Q, r ** J)) < 1e-14
+    exact = scipy.linalg.expm(sm.A)
+    e1 = P.rel_fro(P.crank_nicolson(P.FLOW_EXP, np.eye(12), sm.A, 1.0, 16), exact)
+    e2 = P.rel_fro(P.crank_nicolson(P.FLOW_EXP, np.eye(12), sm.A, 1.0, 32), exact)
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def test_explicit_euler_fine_propagator_is_the_euler_polynomial():
+    """F with the explicit Euler scheme is (I + h A)^J on the linear flow; first order."""
+    sm = inputs.sym_matrix(10, "exp", 22)
+    f = P.propagator("euler", P.FLOW_EXP, sm.A, 0.5, 8)
+    want = np.linalg.matrix_power(np.eye(10) + (0.5 / 8) * sm.A, 8)
+    assert P.rel_fro(f(np.eye(10)), want) < 1e-14
+    exact = scipy.linalg.expm(sm.A)
+    e1 = P.rel_fro(P.sequential_fine(sm.A, P.FLOW_EXP, 1.0, 4, 64, fine="euler"), exact)
+    e2 = P.rel_fro(P.sequential_fine(sm.A, P.FLOW_EXP, 1.0, 4, 128, fine="euler"), exact)
+    assert 1.8 < e1 / e2 < 2.2
+
+
+@pytest.mark.parametrize("ex", [inputs.PAPER_EX1, inputs.PAPER_EX2])
+def test_paper_examples_converge_to_the_fine_solution_and_the_matrix_function(ex):
+    """Section 2, Examples 1 and 2 (n = 80 Laplacian / 2^10, N = 25, J = 200): parareal with the
+    paper's propagators terminates on the sequential fine solution (finite termination at
+    K = N) and its error measure max|E| / max|A| against the function is the fine scheme's."""
+    A = inputs.paper_example_matrix(ex.example)
+    r = P.parareal(A, ex.flow, ex.T, ex.N, 1, ex.J, ex.N, 0.0, coarse=ex.coarse, fine=ex.fine)
+    seq = P.sequential_fine(A, ex.flow, ex.T, ex.N, ex.J, fine=ex.fine)
+    assert P.paper_norm(r.U[ex.N] - seq, A) < 1e-12
+    ref = closed.inv_lu(A) if ex.flow == P.FLOW_INV else scipy.linalg.expm(A)
+    # explicit Euler with h = 2e-4 on the inverse flow: O(h) error; Crank-Nicolson: O(h^2)
+    assert P.paper_norm(r.U[ex.N] - ref, A if ex.flow == P.FLOW_INV else ref) < (
+        5e-2 if ex.flow == P.FLOW_INV else 1e-6)
+    assert r.dx_history[-1] < 1e-12
+    assert r.dx_history[0] > r.dx_history[min(5, len(r.dx_history) - 1)]
