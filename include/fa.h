@@ -104,7 +104,44 @@ typedef struct {
   int refine_steps;   /* refinement steps on the result (inverse: float64 Newton-Schulz; square
                          root: Newton with the Sylvester equation, see fa_refine); 0 = none */
   int coarse_kind;    /* fa_coarse_kind of G (FA_COARSE_EULER = the paper's forward Euler) */
+  int method;         /* fa_method (FA_METHOD_CLASSICAL = Algorithm 1) */
+  double span_drop;   /* FA_METHOD_MODIFIED: a block joins the space when its norm after the
+                         Gram-Schmidt sweeps exceeds span_drop times its norm (0 = the default:
+                         1e-12 for float64 F, 1e-7 for the BF16 forms) */
+  int max_basis;      /* FA_METHOD_MODIFIED: capacity of the space in blocks, <= 4096 (0 = the
+                         default (N + 1) min(max_iters, 3)); blocks beyond it are left to G.
+                         The workspace holds two float64 n x n matrices per block. */
+  int fine_scheme;    /* fa_scheme of F's fine_steps steps per slice (0 = classical RK4) */
+  int coarse_scheme;  /* fa_scheme of G's coarse_steps steps per slice (0 = forward Euler) */
 } fa_problem_desc;
+
+/* Time-stepping schemes of the propagators (Section 2: "any time marching scheme"; its
+ * Examples 1 and 2 use explicit Euler and Crank-Nicolson propagators).
+ * FA_SCHEME_DEFAULT  classical RK4 for F, forward Euler for G.
+ * FA_SCHEME_RK4      classical RK4 (F only).
+ * FA_SCHEME_EULER    explicit (forward) Euler, X <- X + h Fl(X).
+ * FA_SCHEME_CN       Crank-Nicolson, exponential flow only: (I - h/2 A) X' = (I + h/2 A) X,
+ *                    applied as X' = X + h M X with M = (I - h/2 A)^{-1} A formed once per
+ *                    matrix by a float64 Gauss-Jordan solve on the GPU. */
+typedef enum {
+  FA_SCHEME_DEFAULT = 0,
+  FA_SCHEME_RK4 = 1,
+  FA_SCHEME_EULER = 2,
+  FA_SCHEME_CN = 3
+} fa_scheme;
+
+/* Parareal method.
+ * FA_METHOD_CLASSICAL  Algorithm 1 (Section 2).
+ * FA_METHOD_MODIFIED   Algorithm 3 (Section 3), for linear homogeneous flows (the exponential
+ *                      flow): every iteration enlarges a space S^k = Span(S^{k-1}, U^k_0 .. U^k_N)
+ *                      with globalQR (Algorithm 2: Gram-Schmidt in the Frobenius inner product,
+ *                      here two sweeps per block, a block removed when its reduced norm is below
+ *                      span_drop times its norm), runs F on the new basis blocks only (all of
+ *                      them at once, in the fine sweep's arithmetic), and updates sequentially
+ *                      U_{n+1} = sum_i alpha_i F(Q_i) + G(U_n - sum_i alpha_i Q_i),
+ *                      alpha_i = <U_n, Q_i>_F (F is linear, so the first term is F(P U_n)).  The
+ *                      basis, its fine images and the update are float64. */
+typedef enum { FA_METHOD_CLASSICAL = 0, FA_METHOD_MODIFIED = 1 } fa_method;
 
 typedef struct {
   int iters;           /* fine sweeps performed */
@@ -119,6 +156,8 @@ typedef struct {
                           because the convergence measure grew (0 = never) */
   int coef_fallbacks;  /* learned G: coarse steps whose network output was not finite (Euler used) */
   int records;         /* pair records written by the recorder (fa_plan_set_recorder) */
+  int basis_dim;       /* FA_METHOD_MODIFIED: blocks in the final space */
+  int fine_blocks;     /* matrices propagated by F in all (classical: iterations x N) */
 } fa_report;
 
 /* Coarse propagator G.

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfa.so")
-SOURCES = ["fa_tc.cu", "fa_f64.cu", "fa_api.cu", "fa_noalloc.cu", "fa_learned.cu", "fa_refine.cu"]
+SOURCES = ["fa_tc.cu", "fa_f64.cu", "fa_api.cu", "fa_noalloc.cu", "fa_learned.cu", "fa_refine.cu",
+           "fa_krylov.cu", "fa_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -167,6 +167,25 @@ struct fa_plan_s {
   float *qinv(int par) const { return qbuf + (static_cast<size_t>(par) * 2) * d.N * qT * qT; }
   float *qamax(int par) const { return qbuf + (static_cast<size_t>(par) * 2 + 1) * d.N * qT * qT; }
 
+  // modified parareal (Algorithm 3): the F-orthonormal basis Q of the space, the fine images
+  // F(Q_i), reduction partials and the projection coefficients
+  bool modified = false;
+  int cap = 0;                   // capacity of the space in blocks
+  double drop = 0.0;             // removal threshold of globalQR
+  double *Qb = nullptr, *FQb = nullptr, *kpart = nullptr, *apart = nullptr, *alpha = nullptr;
+
+  // time-stepping schemes (FA_SCHEME_*) of F and G; with Crank-Nicolson the exponential flow's
+  // products use the step matrices M = (I - h/2 A)^{-1} A (fine) and (I - dt/2 A)^{-1} A
+  // (coarse) in place of A
+  int fsch = FA_SCHEME_RK4, csch = FA_SCHEME_EULER;
+  double *MF64 = nullptr, *MG64 = nullptr, *aug = nullptr;
+  __nv_bfloat16 *AopF = nullptr, *AopG = nullptr;
+  CUtensorMap tmAF{}, tmAG{};
+  const CUtensorMap &fine_tmA() const { return fsch == FA_SCHEME_CN ? tmAF : tmA; }
+  const CUtensorMap &coarse_tmA() const { return csch == FA_SCHEME_CN ? tmAG : tmA; }
+  const double *fine_A64() const { return fsch == FA_SCHEME_CN ? MF64 : A64; }
+  const double *coarse_A64() const { return csch == FA_SCHEME_CN ? MG64 : A64; }
+
   bool needs_l() const { return d.flow != FA_FLOW_EXP; }  // Y in L form (left factor)
 };
 
@@ -259,6 +278,18 @@ size_t carve(fa_plan_s *p, char *base) {
     p->Lt = c.take<__nv_bfloat16>(3 * p->strideS);
     p->Lq = c.take<__nv_bfloat16>(3 * p->strideS);
     p->Lpq = c.take<__nv_bfloat16>(3 * p->strideS);
+  }
+  if (p->fsch == FA_SCHEME_CN) p->MF64 = c.take<double>(nn);
+  if (p->csch == FA_SCHEME_CN) p->MG64 = c.take<double>(nn);
+  if (p->fsch == FA_SCHEME_CN || p->csch == FA_SCHEME_CN) p->aug = c.take<double>(2 * nn);
+  if (p->mixed && p->fsch == FA_SCHEME_CN) p->AopF = c.take<__nv_bfloat16>(tl * p->strideA);
+  if (p->cmixed && p->csch == FA_SCHEME_CN) p->AopG = c.take<__nv_bfloat16>(tl * p->strideA);
+  if (p->modified) {
+    p->Qb = c.take<double>(static_cast<size_t>(p->cap) * nn);
+    p->FQb = c.take<double>(static_cast<size_t>(p->cap) * nn);
+    p->kpart = c.take<double>(3 * static_cast<size_t>(fa::kKrylovBlocks));
+    p->apart = c.take<double>(static_cast<size_t>(p->cap) * fa::kKrylovBlocks);
+    p->alpha = c.take<double>(static_cast<size_t>(p->cap));
   }
   p->probes = c.take<uint8_t>(static_cast<size_t>(d.n));
   p->mstats = c.take<double>(8);
@@ -366,6 +397,8 @@ fa_status encode_all(fa_plan_s *p) {
     FA_TRY(encode(&p->tmLpq, p->Lpq, n, ldp, 1, 3, p->strideS, TC_BM));
   }
   if (p->Aop) FA_TRY(encode(&p->tmA, p->Aop, n, ldp, 1, tl, p->strideA, TC_BM));
+  if (p->AopF) FA_TRY(encode(&p->tmAF, p->AopF, n, ldp, 1, tl, p->strideA, TC_BM));
+  if (p->AopG) FA_TRY(encode(&p->tmAG, p->AopG, n, ldp, 1, tl, p->strideA, TC_BM));
   if (p->mixed && !p->fp8) {
     for (int k = 0; k < 2; ++k) {
       FA_TRY(encode(&p->tmYr[k], p->Yr[k], n, ldp, N, tr, p->strideY, TC_BN));
@@ -491,14 +524,16 @@ fa_status fine_sweep_fp8(fa_plan_s *p, const double *U, double *out, const doubl
   return FA_OK;
 }
 
-// F on every slice: out = F(U_b) (g_old == null) or F(U_b) - g_old_b.
-fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g_old) {
+// F on every slice: out = F(U_b) (g_old == null) or F(U_b) - g_old_b, for b < nb (nb < 0: all
+// N slices; at most N, the capacity of the fine state).
+fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g_old, int nb = -1) {
   if (p->fp8) return fine_sweep_fp8(p, U, out, g_old);
   const fa_problem_desc &d = p->d;
-  const int n = d.n, N = d.N, J = d.fine_steps;
+  const int n = d.n, N = nb < 0 ? d.N : nb, J = d.fine_steps;
+  const double h = d.T / static_cast<double>(d.N) / static_cast<double>(J);
   const size_t nn = p->nn;
-  const double h = d.T / static_cast<double>(N) / static_cast<double>(J);
   const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  if (N <= 0) return FA_OK;
   if (p->mixed) {
     FA_CUDA(fa::launch_load_state(U, N, n, p->ldp, p->x_hi, p->x_lo, p->Yl[0],
                                   p->needs_l() ? tl : 0, p->strideY, p->Yr[0], tr, p->strideY,
@@ -510,8 +545,12 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
                             p->stream));
   }
   int cur = 0;
+  // RK4: four stage launches per step; explicit Euler and Crank-Nicolson: one explicit step
+  // X <- X + h K per launch (the stage-4 epilogue with acc = 0 and h in place of h/6), K = Fl(X)
+  // or, for Crank-Nicolson, M X
+  const bool rk4 = p->fsch == FA_SCHEME_RK4;
   for (int j = 0; j < J; ++j) {
-    for (int s = 1; s <= 4; ++s) {
+    for (int s = rk4 ? 1 : 4; s <= 4; ++s) {
       const bool last = (j == J - 1 && s == 4);
       EpiParams e = base_epi(p);
       e.mode = fa::EPI_STAGE;
@@ -519,6 +558,7 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
       e.last = last ? 1 : 0;
       e.h = h;
       e.ch = (s == 3) ? h : (s < 3 ? 0.5 * h : 0.0);
+      e.euler_step = rk4 ? 0 : 1;
       e.f_out = out;
       e.g_old = g_old;
       if (p->mixed) {
@@ -533,7 +573,7 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
         e.terms_l = p->needs_l() ? tl : 0;
         e.term_stride_r = e.term_stride_l = p->strideY;
         if (d.flow == FA_FLOW_EXP) {
-          FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, N, 0, 1, e)));
+          FA_TRY(tc(p, p->fine_tmA(), p->tmYr[cur], tc_params(p, N, 0, 1, e)));
         } else if (d.flow == FA_FLOW_SQRT) {
           FA_TRY(tc(p, p->tmYl[cur], p->tmYr[cur], tc_params(p, N, 1, 1, e)));
         } else {
@@ -552,7 +592,7 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
         e.out64 = p->Y64[cur ^ 1];
         const double *Y = p->Y64[cur];
         if (d.flow == FA_FLOW_EXP) {
-          FA_TRY(f64(p, p->A64, 0, Y, nn, N, e));
+          FA_TRY(f64(p, p->fine_A64(), 0, Y, nn, N, e));
         } else if (d.flow == FA_FLOW_SQRT) {
           FA_TRY(f64(p, Y, nn, Y, nn, N, e));
         } else {
@@ -580,7 +620,7 @@ fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
     e.a_hi = p->a_hi;
     e.a_lo = p->a_lo;
     if (d.flow == FA_FLOW_EXP) {
-      FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+      FA_TRY(tc(p, p->coarse_tmA(), p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
     } else if (d.flow == FA_FLOW_SQRT) {
       FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
     } else {
@@ -595,7 +635,7 @@ fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
   } else {
     e.a64 = p->A64;
     if (d.flow == FA_FLOW_EXP) {
-      FA_TRY(f64(p, p->A64, 0, vin, 0, 1, e));
+      FA_TRY(f64(p, p->coarse_A64(), 0, vin, 0, 1, e));
     } else if (d.flow == FA_FLOW_SQRT) {
       FA_TRY(f64(p, vin, 0, vin, 0, 1, e));
     } else {
@@ -1316,6 +1356,193 @@ fa_status batch_iteration(fa_batch_s *b) {
   return FA_OK;
 }
 
+// ---- modified parareal (Algorithm 3) ---------------------------------------------------------
+
+// Sum of kKrylovBlocks partials read back to the host (fixed order).
+double host_sum(const double *h) {
+  double s = 0.0;
+  for (int b = 0; b < fa::kKrylovBlocks; ++b) s += h[b];
+  return s;
+}
+
+// globalQR step (Algorithm 2) for one block z against the basis Q_0 .. Q_{d-1}: two modified
+// Gram-Schmidt sweeps on a copy q, then r = ||q||_F; the block joins the basis as q / r when
+// r > drop ||z||_F and the space has room.  Returns through *kept.
+fa_status gs_extend(fa_plan_s *p, const double *z, int *d, bool *kept) {
+  const size_t nn = p->nn;
+  double *q = p->Xout;
+  double *pz = p->kpart, *pa = p->kpart + fa::kKrylovBlocks, *pb = pa + fa::kKrylovBlocks;
+  FA_CUDA(cudaMemcpyAsync(q, z, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  FA_CUDA(fa::launch_gs_step(q, nullptr, nullptr, nullptr, nn, pz, p->stream));   // ||z||^2
+  const int dd = *d;
+  const double *prev = nullptr;
+  double *pin = pa, *pout = pb;
+  for (int pass = 0; pass < 2 && dd > 0; ++pass) {
+    for (int j = 0; j < dd; ++j) {
+      const double *next = p->Qb + static_cast<size_t>(j) * nn;
+      FA_CUDA(fa::launch_gs_step(q, prev, pin, next, nn, pout, p->stream));
+      prev = next;
+      std::swap(pin, pout);
+    }
+  }
+  double *pr = pz;   // dd == 0: the reduced block is z itself
+  if (dd > 0) {
+    FA_CUDA(fa::launch_gs_step(q, prev, pin, nullptr, nn, pout, p->stream));       // ||q||^2
+    pr = pout;
+  }
+  double hz[fa::kKrylovBlocks], hr[fa::kKrylovBlocks];
+  FA_CUDA(cudaMemcpyAsync(hz, pz, sizeof(hz), cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaMemcpyAsync(hr, pr, sizeof(hr), cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaStreamSynchronize(p->stream));
+  const double zn = std::sqrt(host_sum(hz)), r = std::sqrt(host_sum(hr));
+  if (!std::isfinite(zn) || !std::isfinite(r))
+    return set_err(FA_ERR_NONFINITE, "non-finite block in the parareal space");
+  *kept = r > p->drop * zn && r > 0.0 && dd < p->cap;
+  if (*kept) {
+    FA_CUDA(fa::launch_scale_copy(q, 1.0 / r, nn, p->Qb + static_cast<size_t>(dd) * nn, p->stream));
+    *d = dd + 1;
+  }
+  return FA_OK;
+}
+
+// Sequential update of Algorithm 3 (eq. eq_update): for n = 0..N-1,
+//   alpha = Q^T <> U_n,  R = U_n - sum alpha_i Q_i,  W = sum alpha_i F(Q_i),
+//   U_{n+1} = G(R) + W (forward-Euler substeps on R, W added on the last one),
+// in place on p->U with the convergence norms against the previous iterate.
+fa_status modified_update(fa_plan_s *p, int d) {
+  const fa_problem_desc &d_ = p->d;
+  const int N = d_.N, m = d_.coarse_steps;
+  const size_t nn = p->nn;
+  const double dt = d_.T / static_cast<double>(N) / static_cast<double>(m);
+  const int tl = p->ps.terms_l, tr = p->ps.terms_r;
+  double *R = p->R1, *W = p->R2;
+  const int tiles = p->part_tiles;
+  for (int s = 0; s < N; ++s) {
+    const double *V = p->U + static_cast<size_t>(s) * nn;
+    FA_CUDA(fa::launch_project_alpha(V, p->Qb, nn, d, p->apart, p->alpha, p->stream));
+    FA_CUDA(fa::launch_project_combine(V, p->Qb, p->FQb, p->alpha, d, nn, R, W, p->stream));
+    int cur = 0;
+    if (p->cmixed) FA_TRY(split_coarse(p, R, 0));
+    for (int sub = 0; sub < m; ++sub) {
+      const bool last = (sub == m - 1);
+      const double *vin = (sub == 0) ? R : p->Vtmp[(sub - 1) & 1];
+      double *vout = last ? p->U + static_cast<size_t>(s + 1) * nn : p->Vtmp[sub & 1];
+      EpiParams e = base_epi(p);
+      e.mode = fa::EPI_EULER;
+      e.dt = dt;
+      e.v_in = vin;
+      e.v_out = vout;
+      e.euler_last = last ? 1 : 0;
+      if (last) {
+        e.g_out = p->Gnew + static_cast<size_t>(s) * nn;   // G(R): not needed later
+        e.d_in = W;
+        e.u_old = p->U + static_cast<size_t>(s + 1) * nn;
+        e.norm_part = p->part + static_cast<size_t>(s) * tiles * 2;
+      }
+      if (p->cmixed) {
+        e.out_r = p->Vr[cur ^ 1];
+        e.out_l = p->Vl[cur ^ 1];
+        e.terms_r = tr;
+        e.terms_l = p->needs_l() ? tl : 0;
+        e.term_stride_r = e.term_stride_l = p->strideV;
+      }
+      FA_TRY(euler_gemm(p, cur, vin, e));
+      if (p->cmixed) cur ^= 1;
+    }
+  }
+  FA_CUDA(fa::launch_reduce_norms(p->part, N, tiles, p->norms, p->stream));
+  FA_CUDA(fa::launch_max_ratio(p->norms, N, p->dx, p->err, p->stream));
+  return FA_OK;
+}
+
+// The whole modified solve (matrix already set): Step 0, then per iteration the space's
+// enlargement, F on the new blocks, and the sequential update.
+fa_status modified_solve(fa_plan_s *p, const double *dX0, double *dXout, fa_report *r) {
+  const fa_problem_desc &d = p->d;
+  const size_t nn = p->nn;
+  cudaEvent_t ev[4];
+  for (auto &e : ev) FA_CUDA(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  FA_CUDA(cudaEventRecord(ev[0], p->stream));
+  if (dX0) {
+    FA_CUDA(cudaMemcpyAsync(p->U, dX0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    FA_CUDA(fa::launch_identity(p->U, d.n, p->stream));
+  }
+  // Step 0 (eq. eqStep0): the coarse sweep
+  FA_TRY(coarse_sweep(p, p->U, nullptr, p->U, p->Gold, nullptr, nullptr));
+  FA_CUDA(cudaEventRecord(ev[1], p->stream));
+  FA_CUDA(cudaEventSynchronize(ev[1]));
+  float ms = 0.f;
+  FA_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+  double t_init = ms, t_fine = 0.0, t_coarse = 0.0;
+  int basis = 0, iters = 0, fine_blocks = 0;
+  bool converged = false;
+  double dx = INFINITY;
+  for (int k = 0; k < d.max_iters; ++k) {
+    // S^k = Span(S^{k-1}, U^k_0 .. U^k_N): globalQR of [Q, U_0, ..., U_N] (the old basis is
+    // kept and completed)
+    FA_CUDA(cudaEventRecord(ev[1], p->stream));
+    const int d0 = basis;
+    for (int s = 0; s <= d.N && basis < p->cap; ++s) {
+      bool kept = false;
+      FA_TRY(gs_extend(p, p->U + static_cast<size_t>(s) * nn, &basis, &kept));
+    }
+    // F on the new blocks only, all at once (in chunks of the fine state's N slices)
+    for (int c = d0; c < basis; c += d.N) {
+      const int cnt = basis - c < d.N ? basis - c : d.N;
+      FA_TRY(fine_sweep(p, p->Qb + static_cast<size_t>(c) * nn, p->FQb + static_cast<size_t>(c) * nn,
+                        nullptr, cnt));
+    }
+    fine_blocks += basis - d0;
+    FA_CUDA(cudaEventRecord(ev[2], p->stream));
+    FA_TRY(modified_update(p, basis));
+    FA_CUDA(cudaEventRecord(ev[3], p->stream));
+    FA_CUDA(cudaMemcpyAsync(&dx, p->dx, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    FA_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+    t_fine += ms;
+    FA_CUDA(cudaEventElapsedTime(&ms, ev[2], ev[3]));
+    t_coarse += ms;
+    ++iters;
+    if (r && r->dx_history) r->dx_history[k] = dx;
+    if (!std::isfinite(dx)) break;
+    if (dx < d.tol) {
+      converged = true;
+      break;
+    }
+  }
+  FA_CUDA(cudaMemcpyAsync(dXout, p->U + static_cast<size_t>(d.N) * nn, nn * sizeof(double),
+                          cudaMemcpyDeviceToDevice, p->stream));
+  const fa_status es = read_err(p);
+  if (r) {
+    r->iters = iters;
+    r->converged = converged ? 1 : 0;
+    r->last_dx = dx;
+    r->t_init_ms = t_init;
+    r->t_fine_ms = t_fine;
+    r->t_coarse_ms = t_coarse;
+    r->t_refine_ms = 0.0;
+    r->g_fallback_iter = 0;
+    r->coef_fallbacks = 0;
+    r->records = 0;
+    r->basis_dim = basis;
+    r->fine_blocks = fine_blocks;
+  }
+  if (es != FA_OK) return es;
+  if (!std::isfinite(dx))
+    return set_err(FA_ERR_NONFINITE, "non-finite convergence measure at iteration %d", iters);
+  if (!converged && d.tol > 0.0)
+    return set_err(FA_ERR_NOT_CONVERGED, "tolerance %.3g not reached in %d iterations (dx %.3g)",
+                   d.tol, iters, dx);
+  return FA_OK;
+}
+
 }  // namespace
 
 // ---- C ABI -----------------------------------------------------------------------------------
@@ -1348,6 +1575,33 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
     return set_err(FA_ERR_ARG, "unknown coarse kind %d", d->coarse_kind);
   if (d->fine_dtype == FA_FP8E4M3 && d->flow != FA_FLOW_SQRT)
     return set_err(FA_ERR_UNSUPPORTED, "FA_FP8E4M3 operands are implemented for the square-root flow");
+  if (d->method != FA_METHOD_CLASSICAL && d->method != FA_METHOD_MODIFIED)
+    return set_err(FA_ERR_ARG, "unknown method %d", d->method);
+  if (d->method == FA_METHOD_MODIFIED) {
+    if (d->flow != FA_FLOW_EXP)
+      return set_err(FA_ERR_UNSUPPORTED,
+                     "the modified parareal is for linear homogeneous flows (the exponential flow)");
+    if (d->coarse_kind != FA_COARSE_EULER)
+      return set_err(FA_ERR_UNSUPPORTED, "the modified parareal uses the forward-Euler G");
+    if (d->max_basis < 0 || d->max_basis > 4096)
+      return set_err(FA_ERR_ARG, "max_basis = %d out of range [0, 4096]", d->max_basis);
+    if (!(d->span_drop >= 0.0) || !std::isfinite(d->span_drop))
+      return set_err(FA_ERR_ARG, "span_drop must be finite and >= 0");
+  }
+  if (d->fine_scheme < FA_SCHEME_DEFAULT || d->fine_scheme > FA_SCHEME_CN)
+    return set_err(FA_ERR_ARG, "unknown fine scheme %d", d->fine_scheme);
+  if (d->coarse_scheme != FA_SCHEME_DEFAULT && d->coarse_scheme != FA_SCHEME_EULER &&
+      d->coarse_scheme != FA_SCHEME_CN)
+    return set_err(d->coarse_scheme == FA_SCHEME_RK4 ? FA_ERR_UNSUPPORTED : FA_ERR_ARG,
+                   "coarse scheme %d: G is forward Euler or Crank-Nicolson", d->coarse_scheme);
+  if ((d->fine_scheme == FA_SCHEME_CN || d->coarse_scheme == FA_SCHEME_CN) &&
+      d->flow != FA_FLOW_EXP)
+    return set_err(FA_ERR_UNSUPPORTED, "Crank-Nicolson propagators are for the exponential flow");
+  if ((d->fine_scheme > FA_SCHEME_RK4 || d->coarse_scheme == FA_SCHEME_CN) &&
+      (d->fine_dtype == FA_FP8E4M3 || d->coarse_kind != FA_COARSE_EULER))
+    return set_err(FA_ERR_UNSUPPORTED,
+                   "explicit-Euler and Crank-Nicolson schemes need BF16 or float64 products and "
+                   "the Euler coarse kind");
   if (d->coarse_kind == FA_COARSE_LEARNED) {
     if (d->flow == FA_FLOW_SQRT)
       return set_err(FA_ERR_UNSUPPORTED,
@@ -1382,6 +1636,16 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   p->nn = static_cast<size_t>(d->n) * d->n;
   p->learned = d->coarse_kind == FA_COARSE_LEARNED;
   p->learned_active = p->learned;
+  p->fsch = d->fine_scheme == FA_SCHEME_DEFAULT ? FA_SCHEME_RK4 : d->fine_scheme;
+  p->csch = d->coarse_scheme == FA_SCHEME_DEFAULT ? FA_SCHEME_EULER : d->coarse_scheme;
+  p->modified = d->method == FA_METHOD_MODIFIED;
+  if (p->modified) {
+    // default: three iterations' worth of new blocks (the linear flows here need two or three)
+    const long long k = d->max_iters < 1 ? 1 : (d->max_iters < 3 ? d->max_iters : 3);
+    const long long def = (static_cast<long long>(d->N) + 1) * k;
+    p->cap = d->max_basis > 0 ? d->max_basis : static_cast<int>(def < 4096 ? def : 4096);
+    p->drop = d->span_drop > 0.0 ? d->span_drop : (p->mixed ? 1e-7 : 1e-12);
+  }
   p->part_tiles = p->cmixed ? ((d->n + TC_BM - 1) / TC_BM) * ((d->n + TC_BN - 1) / TC_BN)
                             : fa::f64_tiles_per_slice(d->n, 1);
   p->ws_need = carve(p, nullptr);
@@ -1397,6 +1661,9 @@ fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
     return set_err(FA_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", bytes, p->ws_need);
   if (reinterpret_cast<uintptr_t>(ws) & 255)
     return set_err(FA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  // the plan's device current on this thread (tensor maps are encoded through the driver API,
+  // which needs a current context; a thread that made no runtime call yet has none)
+  FA_CUDA(cudaSetDevice(p->device));
   p->ws = static_cast<char *>(ws);
   carve(p, p->ws);
   p->matrix_set = false;
@@ -1419,6 +1686,24 @@ fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA) {
   FA_CUDA(fa::launch_check_finite(p->A64, nn, p->err, p->stream));
   p->mstats_valid = false;
   if (p->B64) FA_CUDA(fa::launch_i_minus(p->A64, n, p->B64, p->stream));
+  {
+    // Crank-Nicolson step matrices M = (I - c A)^{-1} A, c = half the step
+    const fa_problem_desc &d = p->d;
+    const double hF = d.T / d.N / d.fine_steps, hG = d.T / d.N / d.coarse_steps;
+    const int tl = p->ps.terms_l;
+    if (p->MF64) {
+      FA_CUDA(fa::launch_cn_matrix(p->A64, n, 0.5 * hF, p->aug, p->MF64, p->err, p->stream));
+      if (p->AopF)
+        FA_CUDA(fa::launch_split_terms(p->MF64, 1, n, p->ldp, p->AopF, tl, p->strideA, nullptr,
+                                       0, 0, 0, p->stream));
+    }
+    if (p->MG64) {
+      FA_CUDA(fa::launch_cn_matrix(p->A64, n, 0.5 * hG, p->aug, p->MG64, p->err, p->stream));
+      if (p->AopG)
+        FA_CUDA(fa::launch_split_terms(p->MG64, 1, n, p->ldp, p->AopG, tl, p->strideA, nullptr,
+                                       0, 0, 0, p->stream));
+    }
+  }
   if (p->mixed || p->cmixed) {
     const int tl = p->ps.terms_l;
     if (p->d.flow == FA_FLOW_EXP)
@@ -1476,6 +1761,10 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
     return set_err(FA_ERR_ARG, "fa_plan_set_learned has not been called");
   FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
   FA_CUDA(cudaMemsetAsync(p->fallbacks, 0, sizeof(int), p->stream));
+  if (p->modified) {
+    FA_TRY(fa_plan_set_matrix(p, dA));
+    return modified_solve(p, dX0, dXout, r);
+  }
   p->learned_active = p->learned;
   p->rec_count = 0;
   int g_fallback_iter = 0;
@@ -1576,6 +1865,8 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
     r->g_fallback_iter = g_fallback_iter;
     r->coef_fallbacks = coef_fb;
     r->records = p->rec_count;
+    r->basis_dim = 0;
+    r->fine_blocks = iters * d.N;
     r->iters = iters;
     r->converged = converged ? 1 : 0;
     r->last_dx = dx;
@@ -1813,6 +2104,7 @@ fa_status fa_batch_bind_workspace(fa_batch_t b, void *d_ws, size_t bytes) {
     return set_err(FA_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", bytes, b->ws_need);
   if (reinterpret_cast<uintptr_t>(d_ws) & 255)
     return set_err(FA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  FA_CUDA(cudaSetDevice(b->plans[0]->device));
   b->ws = static_cast<char *>(d_ws);
   b->d_segs = reinterpret_cast<fa::TcSegment *>(b->ws + b->seg_off);
   b->d_norm = reinterpret_cast<fa::BatchNorm *>(b->ws + b->norm_off);

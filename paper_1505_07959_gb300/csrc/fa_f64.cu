@@ -35,7 +35,7 @@ __device__ __forceinline__ void epi_f64(const EpiParams &e, int b, int i, int j,
         ac[g] = ac[g] + 2.0 * K;
         e.out64[g] = X[g] + e.ch * K;
       } else {
-        const double Xn = X[g] + (e.h / 6.0) * (ac[g] + K);
+        const double Xn = e.euler_step ? X[g] + e.h * K : X[g] + (e.h / 6.0) * (ac[g] + K);
         X[g] = Xn;
         if (e.last) {
           e.f_out[g] = e.g_old ? Xn - e.g_old[g] : Xn;

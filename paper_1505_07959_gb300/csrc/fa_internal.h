@@ -88,6 +88,8 @@ struct EpiParams {
   double *store_out;
   const double *store_add;
   int *err;                     // device error word
+  int euler_step;               // EPI_STAGE with stage 4: an explicit step X <- X + h K (the
+                                // explicit-Euler and Crank-Nicolson fine schemes), no acc read
 };
 
 // One problem of a ragged (multi-problem) tensor-core launch: its tensor maps, epilogue
@@ -281,6 +283,30 @@ cudaError_t launch_coarse_coef(const float *P, const double *part, int n, int sl
                                double dT, const double *mstats, float *coef, int *fallbacks,
                                cudaStream_t s);
 cudaError_t launch_combine(const CombineArgs &a, int blocks, cudaStream_t s);
+
+// --- modified parareal (fa_krylov.cu) ---
+constexpr int kKrylovBlocks = 304;   // fixed grid of the reductions (2 x 152 SMs)
+// One Gram-Schmidt step on q: with prev, q -= c prev where c sums part_in[0 .. kKrylovBlocks);
+// part_out[block] = partial <q, next> (or <q, q> when next is null).
+cudaError_t launch_gs_step(double *q, const double *prev, const double *part_in,
+                           const double *next, size_t count, double *part_out, cudaStream_t s);
+// out = scale q
+cudaError_t launch_scale_copy(const double *q, double scale, size_t count, double *out,
+                              cudaStream_t s);
+// alpha[j] = <V, Q_j> for j < d (Q: d consecutive matrices of `count` elements); part holds
+// d x kKrylovBlocks partial sums.
+cudaError_t launch_project_alpha(const double *V, const double *Q, size_t count, int d,
+                                 double *part, double *alpha, cudaStream_t s);
+// R = V - sum_j alpha_j Q_j, W = sum_j alpha_j FQ_j.
+cudaError_t launch_project_combine(const double *V, const double *Q, const double *FQ,
+                                   const double *alpha, int d, size_t count, double *R, double *W,
+                                   cudaStream_t s);
+
+// --- Crank-Nicolson step matrices (fa_solve.cu) ---
+// M = (I - c A)^{-1} A by Gauss-Jordan elimination with partial pivoting on aug = [I - c A | A]
+// (scratch of 2 n^2 doubles); a zero pivot sets *err = FA_ERR_NONFINITE.
+cudaError_t launch_cn_matrix(const double *A, int n, double c, double *aug, double *M, int *err,
+                             cudaStream_t s);
 
 // --- square-root refinement helpers (fa_refine.cu) ---
 constexpr int kDevNormBlocks = 256;

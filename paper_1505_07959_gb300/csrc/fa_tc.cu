@@ -165,7 +165,9 @@ __device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, in
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t base = b * nn + static_cast<size_t>(j0) * n + i;   // column-major (i, j0)
   const float ch = static_cast<float>(e.ch);
-  const float h6 = static_cast<float>(e.h / 6.0);
+  // an explicit step (X + h K) is the stage-4 update with acc = 0 and h in place of h / 6
+  const bool ex = STAGE == 4 && e.euler_step;
+  const float h6 = static_cast<float>(ex ? e.h : e.h / 6.0);
   float *__restrict__ xhp = e.x_hi;
   float *__restrict__ xlp = e.x_lo;
   float *__restrict__ acp = e.acc;
@@ -179,7 +181,7 @@ __device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, in
       const size_t c = base + static_cast<size_t>(GW * g + u) * n;
       const bool ok = u < gcnt;
       xh[u] = ok ? xhp[c] : 0.0f;
-      if (STAGE > 1) ac[u] = ok ? acp[c] : 0.0f;
+      if (STAGE > 1) ac[u] = (ok && !ex) ? acp[c] : 0.0f;
       if (STAGE == 4) xl[u] = ok ? xlp[c] : 0.0f;
       K[u] = v[GW * g + u];
       if (SQRT && ok) {

@@ -33,6 +33,10 @@ SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_s
            "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam",
            "fa_batch_autotune", "fa_batch_tuning", "fa_plan_autotune", "fa_plan_tuning"]
 FA_COARSE_EULER, FA_COARSE_LEARNED = 0, 1
+FA_METHOD_CLASSICAL, FA_METHOD_MODIFIED = 0, 1
+FA_SCHEME_DEFAULT, FA_SCHEME_RK4, FA_SCHEME_EULER, FA_SCHEME_CN = 0, 1, 2, 3
+SCHEMES = {"default": FA_SCHEME_DEFAULT, "rk4": FA_SCHEME_RK4, "euler": FA_SCHEME_EULER,
+           "cn": FA_SCHEME_CN}
 FA_MLP_FEATURES, FA_MLP_HIDDEN, FA_MLP_COEFS, FA_MLP_PARAMS = 8, 128, 4, 18196
 FA_RECORD_DOUBLES = 32
 FA_PROBES, FA_PROBE_SEED = 8, 0x150507959
@@ -43,7 +47,10 @@ class fa_problem_desc(ctypes.Structure):
                 ("N", ctypes.c_int), ("coarse_steps", ctypes.c_int), ("fine_steps", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
                 ("fine_dtype", ctypes.c_int), ("coarse_dtype", ctypes.c_int),
-                ("refine_steps", ctypes.c_int), ("coarse_kind", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("coarse_kind", ctypes.c_int),
+                ("method", ctypes.c_int), ("span_drop", ctypes.c_double),
+                ("max_basis", ctypes.c_int), ("fine_scheme", ctypes.c_int),
+                ("coarse_scheme", ctypes.c_int)]
 
 
 class fa_report(ctypes.Structure):
@@ -51,7 +58,8 @@ class fa_report(ctypes.Structure):
                 ("t_init_ms", ctypes.c_double), ("t_fine_ms", ctypes.c_double),
                 ("t_coarse_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double),
                 ("dx_history", ctypes.POINTER(ctypes.c_double)), ("g_fallback_iter", ctypes.c_int),
-                ("coef_fallbacks", ctypes.c_int), ("records", ctypes.c_int)]
+                ("coef_fallbacks", ctypes.c_int), ("records", ctypes.c_int),
+                ("basis_dim", ctypes.c_int), ("fine_blocks", ctypes.c_int)]
 
 
 class FaError(RuntimeError):
@@ -322,7 +330,8 @@ class Plan:
 
     def __init__(self, n, flow, T, N, fine_steps, coarse_steps=1, max_iters=None, tol=0.0,
                  fine_dtype="f64", coarse_dtype=None, refine_steps=0, stream=None,
-                 coarse_kind=FA_COARSE_EULER):
+                 coarse_kind=FA_COARSE_EULER, method=FA_METHOD_CLASSICAL, span_drop=0.0,
+                 max_basis=0, fine_scheme="default", coarse_scheme="default"):
         import torch
 
         self.torch = torch
@@ -333,7 +342,13 @@ class Plan:
                                     fine_steps=fine_steps,
                                     max_iters=N if max_iters is None else max_iters,
                                     tol=float(tol), fine_dtype=fd, coarse_dtype=cd,
-                                    refine_steps=refine_steps, coarse_kind=int(coarse_kind))
+                                    refine_steps=refine_steps, coarse_kind=int(coarse_kind),
+                                    method=int(method), span_drop=float(span_drop),
+                                    max_basis=int(max_basis),
+                                    fine_scheme=SCHEMES[fine_scheme] if isinstance(fine_scheme, str)
+                                    else int(fine_scheme),
+                                    coarse_scheme=SCHEMES[coarse_scheme]
+                                    if isinstance(coarse_scheme, str) else int(coarse_scheme))
         self.n, self.N = n, N
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle, self.ws_bytes = fa_plan(self.desc, self.stream.cuda_stream)
@@ -556,4 +571,4 @@ def _report(rep: fa_report, hist, status) -> dict:
             "t_fine_ms": rep.t_fine_ms, "t_coarse_ms": rep.t_coarse_ms,
             "t_refine_ms": rep.t_refine_ms, "status": status,
             "g_fallback_iter": rep.g_fallback_iter, "coef_fallbacks": rep.coef_fallbacks,
-            "records": rep.records}
+            "records": rep.records, "basis_dim": rep.basis_dim, "fine_blocks": rep.fine_blocks}
