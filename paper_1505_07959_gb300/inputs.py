@@ -85,6 +85,26 @@ def laplacian_1d(n: int, scaled: bool = True) -> np.ndarray:
     return a
 
 
+def laplacian_2d(m: int) -> np.ndarray:
+    """The five-point finite-difference Laplacian on an m x m grid (order m^2): tridiag(-1, 4,
+    -1) diagonal blocks coupled by -I.  Section 4, Example 5 inverts it after scaling by its
+    Frobenius norm."""
+    T = 4.0 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+    return np.kron(np.eye(m), T) - np.kron(np.eye(m, k=1) + np.eye(m, k=-1), np.eye(m))
+
+
+def aima_example(m: int = 63, threshold: float = 0.01):
+    """Example 5's inputs: A = L2 / ||L2||_F (L2 the m x m grid Laplacian), X0 = 0, and the
+    initial error estimate e = (A^{-1} with the entries below `threshold` times its largest
+    magnitude set to zero) - X0, the thresholding of the paper's first experiment (the second uses
+    e = A^{-1} exactly: threshold 0).  Returns (A, X0, e)."""
+    L = laplacian_2d(m)
+    A = L / np.linalg.norm(L)
+    Ainv = np.linalg.inv(A)
+    e = np.where(np.abs(Ainv) >= threshold * np.max(np.abs(Ainv)), Ainv, 0.0)
+    return A, np.zeros_like(A), e
+
+
 @dataclasses.dataclass
 class Workload:
     """One parareal problem: flow, matrix family, slices and step counts."""
