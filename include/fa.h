@@ -62,7 +62,14 @@ typedef enum {
   FA_ERR_UNSUPPORTED = 7     /* valid but not supported (e.g. device is not sm_103) */
 } fa_status;
 
-typedef enum { FA_FLOW_INV = 0, FA_FLOW_EXP = 1, FA_FLOW_SQRT = 2 } fa_flow;
+/* FA_FLOW_COS  cos(A) by Algorithm 5 (Section 3, Example 3): A0 = 2^-m A with the smallest m >= 0
+ *              such that 2^-m ||A||_inf <= 1; the block linear flow dU/dt = B U of eq. eqB,
+ *              B = [[0, A0], [-A0, 0]], from U(0) = (0; I) over [0, 1] (so U(1) = (sin A0; cos A0)),
+ *              held as the second block column of an order-2n exponential-flow state
+ *              (X(0) = diag(0, I)) and solved by the plan's method, schemes and dtypes; then
+ *              C <- 2 C^2 - I, m times, in float64.  T must be 1; fine scheme RK4 or explicit
+ *              Euler, forward-Euler G; fa_parareal_solve(_host) are its only compute calls. */
+typedef enum { FA_FLOW_INV = 0, FA_FLOW_EXP = 1, FA_FLOW_SQRT = 2, FA_FLOW_COS = 3 } fa_flow;
 
 /* Arithmetic of the fine and coarse propagators' matrix products.
  * FA_F64     float64 everywhere (SIMT FMA).
@@ -157,6 +164,7 @@ typedef struct {
   int coef_fallbacks;  /* learned G: coarse steps whose network output was not finite (Euler used) */
   int records;         /* pair records written by the recorder (fa_plan_set_recorder) */
   int basis_dim;       /* FA_METHOD_MODIFIED: blocks in the final space */
+  int double_angle_steps; /* FA_FLOW_COS: m of Algorithm 5 */
   int fine_blocks;     /* matrices propagated by F in all (classical: iterations x N) */
 } fa_report;
 
@@ -435,6 +443,25 @@ fa_status fa_mlp_loss_grad(const float *d_params, int batch, const double *d_rec
  * `step` = t >= 1. */
 fa_status fa_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
                       float lr, float beta1, float beta2, float eps, void *stream);
+
+/* ---- Accelerated inverse-matrix approximation (Algorithm 8, Section 4) ------------------
+ *
+ * The steady state of dX/dt = I - A X is A^{-1} (e.g. for SPD A); Section 4 accelerates its
+ * explicit time marching with a control u that starts at e = X~ - X0 (X~ an approximation of
+ * A^{-1}, from a preconditioner) and decays as u' = -A u:
+ *     X^(k+1) = X^(k) + dt (I - A X^(k) + u^(k)),   u^(k+1) = (I - dt A) u^(k).
+ * Each step is one product A [X | u] (two slices sharing the left factor A) whose epilogue
+ * writes both updates and the residual ||I - A X^(k)||_F.
+ *
+ * fa_aima_plan: a plan for order n with products in `dtype` (FA_F64 or a BF16 form; the state
+ * stays float64); bind its workspace with fa_plan_bind_workspace.
+ * fa_aima: `steps` iterations from dX0 with the initial error dE (device n x n float64
+ * row-major); dXout receives X^(steps); h_res (host, steps + 1 doubles, or NULL) receives
+ * ||I - A X^(k)||_F for k = 0..steps.  FA_ERR_ARG for dt <= 0, steps < 0 or steps >= n^2, or a
+ * plan not made by fa_aima_plan.  Synchronises the plan's stream. */
+fa_status fa_aima_plan(fa_plan_t *out, int n, int dtype, void *stream, size_t *workspace_bytes);
+fa_status fa_aima(fa_plan_t p, const double *dA, const double *dX0, const double *dE, double dt,
+                  int steps, double *dXout, double *h_res);
 
 /* Release the plan (not the workspace, which the caller owns). */
 fa_status fa_plan_destroy(fa_plan_t p);

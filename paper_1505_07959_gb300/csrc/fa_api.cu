@@ -186,6 +186,15 @@ struct fa_plan_s {
   const double *fine_A64() const { return fsch == FA_SCHEME_CN ? MF64 : A64; }
   const double *coarse_A64() const { return csch == FA_SCHEME_CN ? MG64 : A64; }
 
+  bool aima = false;             // a plan of fa_aima_plan (Algorithm 8)
+  // FA_FLOW_COS: the order-2n exponential-flow plan of eq. eqB's block flow, and the outer
+  // plan's own buffers (block matrix, start state, result, double-angle iterates, scalar)
+  fa_plan_s *inner = nullptr;
+  size_t inner_ws = 0;
+  double *Bm = nullptr, *X0b = nullptr, *Ub = nullptr, *Cw[2] = {nullptr, nullptr},
+         *scal = nullptr;
+  ~fa_plan_s() { delete inner; }
+
   bool needs_l() const { return d.flow != FA_FLOW_EXP; }  // Y in L form (left factor)
 };
 
@@ -196,6 +205,21 @@ constexpr int TC_BM = 128, TC_BN = 128;
 size_t carve(fa_plan_s *p, char *base) {
   Carver c{base};
   const fa_problem_desc &d = p->d;
+  if (p->inner) {
+    // FA_FLOW_COS: the inner plan's workspace first, then the outer buffers
+    c.take<char>(p->inner_ws);
+    const size_t n2 = 4 * static_cast<size_t>(d.n) * d.n;
+    p->Bm = c.take<double>(n2);
+    p->X0b = c.take<double>(n2);
+    p->Ub = c.take<double>(n2);
+    p->Cw[0] = c.take<double>(static_cast<size_t>(d.n) * d.n);
+    p->Cw[1] = c.take<double>(static_cast<size_t>(d.n) * d.n);
+    p->scal = c.take<double>(4);
+    p->err = c.take<int>(4);
+    p->A64 = c.take<double>(static_cast<size_t>(d.n) * d.n);     // host-buffer solve: A, X
+    p->Xout = c.take<double>(static_cast<size_t>(d.n) * d.n);
+    return c.off + 256;
+  }
   const size_t nn = p->nn;
   const size_t N = static_cast<size_t>(d.N);
   p->U = c.take<double>((N + 1) * nn);
@@ -1549,9 +1573,12 @@ fa_status modified_solve(fa_plan_s *p, const double *dX0, double *dXout, fa_repo
 
 extern "C" {
 
+fa_status cos_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t *ws_bytes);
+
 fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t *ws_bytes) {
   if (!out || !d || !ws_bytes) return set_err(FA_ERR_ARG, "null argument");
   *out = nullptr;
+  if (d->flow == FA_FLOW_COS) return cos_plan(out, d, stream, ws_bytes);
   if (d->n < 1 || d->n > 16384) return set_err(FA_ERR_ARG, "n = %d out of range [1, 16384]", d->n);
   if (d->N < 1) return set_err(FA_ERR_ARG, "N = %d must be >= 1", d->N);
   if (d->fine_steps < 1) return set_err(FA_ERR_ARG, "fine_steps = %d must be >= 1", d->fine_steps);
@@ -1654,6 +1681,167 @@ fa_status fa_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t
   return FA_OK;
 }
 
+// FA_FLOW_COS plans: an inner exponential-flow plan of order 2n for eq. eqB's block flow.
+fa_status cos_plan(fa_plan_t *out, const fa_problem_desc *d, void *stream, size_t *ws_bytes) {
+  if (d->n < 1 || d->n > 8192) return set_err(FA_ERR_ARG, "n = %d out of range [1, 8192]", d->n);
+  if (d->T != 1.0) return set_err(FA_ERR_ARG, "FA_FLOW_COS integrates over [0, 1]: T must be 1");
+  if (d->fine_scheme == FA_SCHEME_CN || d->coarse_scheme == FA_SCHEME_CN)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS uses RK4 or explicit-Euler propagators");
+  if (d->refine_steps != 0) return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS has no refinement");
+  fa_problem_desc d2 = *d;
+  d2.n = 2 * d->n;
+  d2.flow = FA_FLOW_EXP;
+  fa_plan_t inner = nullptr;
+  size_t iws = 0;
+  FA_TRY(fa_plan(&inner, &d2, stream, &iws));
+  fa_plan_s *p = new (std::nothrow) fa_plan_s();
+  if (!p) {
+    delete inner;
+    return set_err(FA_ERR_ARG, "out of host memory");
+  }
+  p->d = *d;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->device = inner->device;
+  p->num_sms = inner->num_sms;
+  p->nn = static_cast<size_t>(d->n) * d->n;
+  p->inner = inner;
+  p->inner_ws = (iws + 255) / 256 * 256;
+  p->ws_need = carve(p, nullptr);
+  *ws_bytes = p->ws_need;
+  *out = p;
+  return FA_OK;
+}
+
+// cos(A) by Algorithm 5 on an FA_FLOW_COS plan.
+fa_status cos_solve(fa_plan_s *p, const double *dA, double *dXout, fa_report *r) {
+  const int n = p->d.n;
+  FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  FA_CUDA(fa::launch_check_finite(dA, p->nn, p->err, p->stream));
+  // step 1: the smallest m >= 0 with 2^-m ||A||_inf <= 1
+  FA_CUDA(fa::launch_inf_norm(dA, n, p->scal, p->stream));
+  double a = 0.0;
+  FA_CUDA(cudaMemcpyAsync(&a, p->scal, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  FA_CUDA(cudaStreamSynchronize(p->stream));
+  if (!std::isfinite(a)) return set_err(FA_ERR_NONFINITE, "non-finite entries in A");
+  int m = 0;
+  double scale = 1.0;
+  while (a > 1.0) {
+    a *= 0.5;
+    scale *= 0.5;
+    ++m;
+  }
+  // steps 2-3: eq. eqB's block flow for A0 = 2^-m A from (0; I), by the inner plan
+  FA_CUDA(fa::launch_cos_block(dA, n, scale, p->Bm, p->X0b, p->stream));
+  const fa_status st = fa_parareal_solve(p->inner, p->Bm, p->X0b, p->Ub, r);
+  if (st != FA_OK && st != FA_ERR_NOT_CONVERGED) return st;
+  // C_0 = cos(A0): the lower-right block; step 4: C <- 2 C^2 - I, m times (float64)
+  FA_CUDA(fa::launch_extract_block(p->Ub, n, n, n, p->Cw[0], p->stream));
+  int cur = 0;
+  for (int i = 0; i < m; ++i) {
+    F64GemmParams g;
+    memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.nb = 1;
+    g.L = p->Cw[cur];
+    g.R = p->Cw[cur];
+    g.epi.mode = fa::EPI_STORE;
+    g.epi.n = n;
+    g.epi.alpha = 2.0;
+    g.epi.beta = -1.0;
+    g.epi.store_out = p->Cw[cur ^ 1];
+    g.epi.err = p->err;
+    FA_CUDA(fa::launch_f64_gemm(g, p->stream));
+    cur ^= 1;
+  }
+  FA_CUDA(cudaMemcpyAsync(dXout, p->Cw[cur], p->nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                          p->stream));
+  if (r) r->double_angle_steps = m;
+  const fa_status es = read_err(p);
+  if (es != FA_OK) return es;
+  return st;
+}
+
+fa_status fa_aima_plan(fa_plan_t *out, int n, int dtype, void *stream, size_t *ws_bytes) {
+  if (!out || !ws_bytes) return set_err(FA_ERR_ARG, "null argument");
+  if (dtype != FA_F64 && !is_mixed(dtype))
+    return set_err(FA_ERR_ARG, "dtype must be FA_F64 or a BF16 form");
+  // the machinery of a two-slice exponential-flow plan: the shared left factor A, the right
+  // factor [X | u] (slices 0 and 1)
+  fa_problem_desc d{};
+  d.n = n;
+  d.flow = FA_FLOW_EXP;
+  d.T = 1.0;
+  d.N = 2;
+  d.coarse_steps = 1;
+  d.fine_steps = 1;
+  d.max_iters = 0;
+  d.fine_dtype = dtype;
+  d.coarse_dtype = dtype;
+  FA_TRY(fa_plan(out, &d, stream, ws_bytes));
+  fa_plan_s *p = *out;
+  p->aima = true;
+  if (!p->mixed) {
+    // residual partials per tile of slice 0 in the two-slice float64 launch
+    p->part_tiles = fa::f64_tiles_per_slice(n, 2);
+    p->ws_need = carve(p, nullptr);
+    *ws_bytes = p->ws_need;
+  }
+  return FA_OK;
+}
+
+fa_status fa_aima(fa_plan_t p, const double *dA, const double *dX0, const double *dE, double dt,
+                  int steps, double *dXout, double *h_res) {
+  FA_TRY(check_ready(p, false));
+  if (!p->aima) return set_err(FA_ERR_ARG, "the plan was not made by fa_aima_plan");
+  if (!dA || !dX0 || !dE || !dXout) return set_err(FA_ERR_ARG, "null pointer");
+  const int n = p->d.n;
+  const size_t nn = p->nn;
+  if (steps < 0 || static_cast<size_t>(steps) + 1 > nn)
+    return set_err(FA_ERR_ARG, "steps = %d out of range [0, n^2 - 1]", steps);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(FA_ERR_ARG, "dt must be finite and > 0");
+  FA_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  FA_TRY(fa_plan_set_matrix(p, dA));
+  // state [X | u] (float64 [2][n][n]) double-buffered in Gold / Gnew; residuals in D
+  double *S[2] = {p->Gold, p->Gnew};
+  double *res = p->D;
+  FA_CUDA(cudaMemcpyAsync(S[0], dX0, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  FA_CUDA(cudaMemcpyAsync(S[0] + nn, dE, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  const int tr = p->ps.terms_r;
+  if (p->mixed)
+    FA_CUDA(fa::launch_split_terms(S[0], 2, n, p->ldp, nullptr, 0, 0, p->Yr[0], tr, p->strideY, 0,
+                                   p->stream));
+  int cur = 0;
+  for (int k = 0; k <= steps; ++k) {
+    EpiParams e = base_epi(p);
+    e.mode = fa::EPI_AIMA;
+    e.last = (k == steps) ? 1 : 0;   // the final launch forms the residual only
+    e.dt = dt;
+    e.x64 = S[cur];
+    e.out64 = S[cur ^ 1];
+    e.norm_part = p->part;
+    if (p->mixed) {
+      e.out_r = p->Yr[cur ^ 1];
+      e.terms_r = tr;
+      e.term_stride_r = p->strideY;
+      FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, 2, 0, 1, e)));
+    } else {
+      FA_TRY(f64(p, p->A64, 0, S[cur], nn, 2, e));
+    }
+    FA_CUDA(fa::launch_reduce_norms(p->part, 1, p->part_tiles, res + 2 * static_cast<size_t>(k),
+                                    p->stream));
+    if (k < steps) cur ^= 1;
+  }
+  FA_CUDA(cudaMemcpyAsync(dXout, S[cur], nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  if (h_res) {
+    std::vector<double> r2(2 * (static_cast<size_t>(steps) + 1));
+    FA_CUDA(cudaMemcpyAsync(r2.data(), res, r2.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    for (int k = 0; k <= steps; ++k) h_res[k] = std::sqrt(r2[2 * static_cast<size_t>(k)]);
+  }
+  return read_err(p);
+}
+
 fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
   if (!p) return set_err(FA_ERR_ARG, "null plan");
   if (!ws) return set_err(FA_ERR_WORKSPACE, "null workspace");
@@ -1664,6 +1852,12 @@ fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
   // the plan's device current on this thread (tensor maps are encoded through the driver API,
   // which needs a current context; a thread that made no runtime call yet has none)
   FA_CUDA(cudaSetDevice(p->device));
+  if (p->inner) {
+    FA_TRY(fa_plan_bind_workspace(p->inner, ws, p->inner->ws_need));
+    p->ws = static_cast<char *>(ws);
+    carve(p, p->ws);
+    return FA_OK;
+  }
   p->ws = static_cast<char *>(ws);
   carve(p, p->ws);
   p->matrix_set = false;
@@ -1677,6 +1871,8 @@ fa_status fa_plan_bind_workspace(fa_plan_t p, void *ws, size_t bytes) {
 }
 
 fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, false));
   if (!dA) return set_err(FA_ERR_ARG, "null A");
   const int n = p->d.n;
@@ -1720,6 +1916,8 @@ fa_status fa_plan_set_matrix(fa_plan_t p, const double *dA) {
 }
 
 fa_status fa_fine_sweep(fa_plan_t p, const double *dU, double *dF) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, true));
   if (!dU || !dF) return set_err(FA_ERR_ARG, "null pointer");
   return fine_sweep(p, dU, dF, nullptr);
@@ -1727,6 +1925,8 @@ fa_status fa_fine_sweep(fa_plan_t p, const double *dU, double *dF) {
 
 fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD, double *dUnew,
                           double *dGnew, double *dNorms, const double *dUold) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, true));
   if (!dU0 || !dUnew || !dGnew) return set_err(FA_ERR_ARG, "null pointer");
   if (dNorms && !dUold) return set_err(FA_ERR_ARG, "dNorms requires dUold");
@@ -1734,6 +1934,8 @@ fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD, doub
 }
 
 fa_status fa_refine(fa_plan_t p, double *dX) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, true));
   if (!dX) return set_err(FA_ERR_ARG, "null pointer");
   if (p->d.flow == FA_FLOW_EXP)
@@ -1745,6 +1947,10 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
                             fa_report *r) {
   FA_TRY(check_ready(p, false));
   if (!dA || !dXout) return set_err(FA_ERR_ARG, "null pointer");
+  if (p->inner) {
+    if (dX0) return set_err(FA_ERR_ARG, "FA_FLOW_COS starts from (0; I): dX0 must be NULL");
+    return cos_solve(p, dA, dXout, r);
+  }
   if (p->d.refine_steps > 0 && p->d.flow == FA_FLOW_EXP)
     return set_err(FA_ERR_UNSUPPORTED, "the exponential flow has no refinement");
   const fa_problem_desc &d = p->d;
@@ -1765,6 +1971,7 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
     FA_TRY(fa_plan_set_matrix(p, dA));
     return modified_solve(p, dX0, dXout, r);
   }
+
   p->learned_active = p->learned;
   p->rec_count = 0;
   int g_fallback_iter = 0;
@@ -1898,6 +2105,8 @@ fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX
 }
 
 fa_status fa_debug_product(fa_plan_t p, const double *dL, const double *dR, double *dC) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, false));
   if (!dL || !dR || !dC) return set_err(FA_ERR_ARG, "null pointer");
   EpiParams e = base_epi(p);
@@ -2301,6 +2510,8 @@ fa_status fa_batch_autotune(fa_batch_t b, const double *const *dA, const char *c
 const char *fa_batch_tuning(fa_batch_t b) { return b ? b->tuning.c_str() : ""; }
 
 fa_status fa_plan_autotune(fa_plan_t p) {
+  if (p && p->inner)
+    return set_err(FA_ERR_UNSUPPORTED, "FA_FLOW_COS plans are solved with fa_parareal_solve only");
   FA_TRY(check_ready(p, true));
   if (p->fp8) {
     p->tuning = "E4M3 operands: the default schedule";

@@ -66,6 +66,18 @@ __device__ __forceinline__ void epi_f64(const EpiParams &e, int b, int i, int j,
       e.v_out[r] = Vn;
       break;
     }
+    case EPI_AIMA: {
+      // Algorithm 8: slice 0 is X, slice 1 the control u (float64, current state in x64, next in
+      // out64); v = (A X)_ij or (A u)_ij.  The residual (I - A X)_ij of the current X is summed.
+      if (b == 0) {
+        const double res = (i == j ? 1.0 : 0.0) - v;
+        s0 += res * res;
+        if (!e.last) e.out64[r] = e.x64[r] + e.dt * (res + e.x64[nn + r]);
+      } else if (!e.last) {
+        e.out64[nn + r] = e.x64[nn + r] - e.dt * v;
+      }
+      break;
+    }
     default:
       e.store_out[b * nn + r] = e.alpha * v + (i == j ? e.beta : 0.0) +
                                 (e.store_add ? e.store_add[b * nn + r] : 0.0);
@@ -130,7 +142,7 @@ __global__ void __launch_bounds__(F64_THREADS)
       if (i < n && j < n) epi_f64(p.epi, gb, i, j, acc[u][w], s0, s1);
     }
 
-  if (p.epi.mode == EPI_EULER && p.epi.u_old != nullptr) {
+  if ((p.epi.mode == EPI_EULER && p.epi.u_old != nullptr) || (p.epi.mode == EPI_AIMA && gb == 0)) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       s0 += __shfl_xor_sync(0xffffffffu, s0, off);

@@ -33,6 +33,7 @@ enum EpiMode : int {
   EPI_EULER = 2,   // forward-Euler substep of G, with the parareal correction on the last one
   EPI_STORE = 3,   // plain float64 store: out = alpha * v + beta * (i == j)
   EPI_TAYLOR = 4,  // a product of a Taylor-term chain: float64 copy (out64) + operand terms
+  EPI_AIMA = 5,    // a step of Algorithm 8 on [X | u] (slices 0 and 1) + the residual norm
 };
 
 // Parameters of the fused epilogue.  One struct serves the tensor-core and the
@@ -307,6 +308,16 @@ cudaError_t launch_project_combine(const double *V, const double *Q, const doubl
 // (scratch of 2 n^2 doubles); a zero pivot sets *err = FA_ERR_NONFINITE.
 cudaError_t launch_cn_matrix(const double *A, int n, double c, double *aug, double *M, int *err,
                              cudaStream_t s);
+
+// --- cosine by Algorithm 5 (fa_solve.cu) ---
+// out[0] = ||A||_inf (largest absolute row sum)
+cudaError_t launch_inf_norm(const double *A, int n, double *out, cudaStream_t s);
+// B = [[0, scale A], [-scale A, 0]] and X0 = diag(0, I), both of order 2n
+cudaError_t launch_cos_block(const double *A, int n, double scale, double *B, double *X0,
+                             cudaStream_t s);
+// out = the n x n block at (r0, c0) of the order-2n matrix U
+cudaError_t launch_extract_block(const double *U, int n, int r0, int c0, double *out,
+                                 cudaStream_t s);
 
 // --- square-root refinement helpers (fa_refine.cu) ---
 constexpr int kDevNormBlocks = 256;

@@ -132,3 +132,82 @@ cudaError_t launch_cn_matrix(const double *A, int n, double c, double *aug, doub
 }
 
 }  // namespace fa
+
+// ---- cosine by Algorithm 5 (Section 3, Example 3) -------------------------------------------
+
+namespace fa {
+
+namespace {
+
+// out[0] = ||A||_inf = max_i sum_j |A_ij| (one block; rows summed in order, maximum in a fixed
+// tree order).
+__global__ void __launch_bounds__(1024) inf_norm_kernel(const double *__restrict__ A, int n,
+                                                         double *out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fabs(A[static_cast<size_t>(i) * n + j]);
+    m = fmax(m, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) t = fmax(t, red[w]);
+    out[0] = t;
+  }
+}
+
+// B = [[0, s A], [-s A, 0]] (order 2n) and X0 = [[0, 0], [0, I]] (eq. eqB from U(0) = (0; I),
+// embedded as the second block column of an order-2n state).
+__global__ void cos_block_kernel(const double *__restrict__ A, int n, double s, double *B,
+                                 double *X0) {
+  const size_t m = 2 * static_cast<size_t>(n), total = m * m;
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t i = t / m, j = t % m;
+    double b = 0.0;
+    if (i < static_cast<size_t>(n) && j >= static_cast<size_t>(n)) b = s * A[i * n + (j - n)];
+    if (i >= static_cast<size_t>(n) && j < static_cast<size_t>(n)) b = -s * A[(i - n) * n + j];
+    B[t] = b;
+    X0[t] = (i == j && i >= static_cast<size_t>(n)) ? 1.0 : 0.0;
+  }
+}
+
+// out (n x n) = the block (r0.., c0..) of the order-2n matrix U.
+__global__ void extract_block_kernel(const double *__restrict__ U, int n, int r0, int c0,
+                                     double *__restrict__ out) {
+  const size_t nn = static_cast<size_t>(n) * n, m = 2 * static_cast<size_t>(n);
+  for (size_t t = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; t < nn;
+       t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t i = t / n, j = t % n;
+    out[t] = U[(r0 + i) * m + c0 + j];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_inf_norm(const double *A, int n, double *out, cudaStream_t s) {
+  inf_norm_kernel<<<1, 1024, 0, s>>>(A, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cos_block(const double *A, int n, double scale, double *B, double *X0,
+                             cudaStream_t s) {
+  cos_block_kernel<<<grid_for(4 * static_cast<size_t>(n) * n), 256, 0, s>>>(A, n, scale, B, X0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_block(const double *U, int n, int r0, int c0, double *out,
+                                 cudaStream_t s) {
+  extract_block_kernel<<<grid_for(static_cast<size_t>(n) * n), 256, 0, s>>>(U, n, r0, c0, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace fa

@@ -277,6 +277,35 @@ __device__ __forceinline__ void stage_chunk(const EpiParams &e, int b, int i, in
   }
 }
 
+// A step of Algorithm 8 (accelerated inverse-matrix approximation) on 32 columns of row i:
+// slice 0 holds X, slice 1 the control u (float64 row-major [2][n][n] in x64), v = (A X) or (A u).
+// X <- X + dt (I - A X + u) and u <- u - dt A u go to out64 with the next product's R-form terms;
+// s0 sums (I - A X)^2, the residual of the current X.  With e.last only the residual is formed.
+__device__ __forceinline__ void aima_chunk(const EpiParams &e, int b, int i, int j0, int cnt,
+                                           const float (&v)[32], double &s0) {
+  const int n = e.n;
+  const size_t nn = static_cast<size_t>(n) * n;
+  const size_t r0 = static_cast<size_t>(i) * n + j0;
+#pragma unroll 4
+  for (int jj = 0; jj < 32; ++jj) {
+    if (jj >= cnt) break;
+    const double p = static_cast<double>(v[jj]);
+    if (b == 0) {
+      const double res = (i == j0 + jj ? 1.0 : 0.0) - p;
+      s0 += res * res;
+      if (!e.last) {
+        const double xn = e.x64[r0 + jj] + e.dt * (res + e.x64[nn + r0 + jj]);
+        e.out64[r0 + jj] = xn;
+        if (e.terms_r) put_r(e, 0, i, j0 + jj, split3_f64(xn));
+      }
+    } else if (!e.last) {
+      const double un = e.x64[nn + r0 + jj] - e.dt * p;
+      e.out64[nn + r0 + jj] = un;
+      if (e.terms_r) put_r(e, 1, i, j0 + jj, split3_f64(un));
+    }
+  }
+}
+
 // Forward-Euler substep G = V + dt Fl(V) on 32 columns of row i (single slice,
 // row-major float64); on the last substep also G_n, the correction
 // V_{n+1} = G_n + D_n and the norm terms.  Writes V's operand terms.
@@ -867,7 +896,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const TileInfo ti_ = tile_info(p, &tmL, &tmR, tile);
       const EpiParams &e = *ti_.epi;
       const int n = e.n;
-      const bool norms = (e.mode == EPI_EULER) && (e.u_old != nullptr);
+      const bool norms = ((e.mode == EPI_EULER) && (e.u_old != nullptr)) || e.mode == EPI_AIMA;
       const int mt = ti_.mt, ntile = ti_.ntile, lb = ti_.lslice, gb = ti_.gb;
       const int i = mt * BM + row;
       const bool kform = drain_forms_k(p, e);   // the finished tile holds K, not the product
@@ -945,6 +974,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           euler_chunk(e, i, j0, cnt, v, s0, s1);
         } else if (e.mode == EPI_TAYLOR) {
           taylor_chunk(e, gb, i, j0, cnt, v);
+        } else if (e.mode == EPI_AIMA) {
+          aima_chunk(e, gb, i, j0, cnt, v, s0);
         } else {
           store_chunk(e, gb, i, j0, cnt, v);
         }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libfa.so")
 
 FA_OK = 0
 FA_ERR_NOT_CONVERGED = 5
-FA_FLOW_INV, FA_FLOW_EXP, FA_FLOW_SQRT = 0, 1, 2
+FA_FLOW_INV, FA_FLOW_EXP, FA_FLOW_SQRT, FA_FLOW_COS = 0, 1, 2, 3
 FA_F64, FA_BF16, FA_BF16X3, FA_BF16X4, FA_BF16X6, FA_FP8E4M3 = 0, 1, 2, 3, 4, 5
 DTYPES = {"f64": FA_F64, "bf16": FA_BF16, "bf16x3": FA_BF16X3, "bf16x4": FA_BF16X4,
           "bf16x6": FA_BF16X6, "fp8e4m3": FA_FP8E4M3}
@@ -29,7 +29,7 @@ SYMBOLS = ["fa_plan", "fa_plan_bind_workspace", "fa_plan_set_matrix", "fa_fine_s
            "fa_launch_count", "fa_launch_count_reset", "fa_batch_plan", "fa_batch_bind_workspace",
            "fa_batch_solve", "fa_batch_destroy", "fa_plan_set_learned", "fa_plan_learned_coefs",
            "fa_learned_records_scratch", "fa_learned_records", "fa_plan_set_recorder",
-           "fa_plan_set_learned_check",
+           "fa_plan_set_learned_check", "fa_aima_plan", "fa_aima",
            "fa_mlp_forward", "fa_mlp_scratch_bytes", "fa_mlp_loss_grad", "fa_mlp_adam",
            "fa_batch_autotune", "fa_batch_tuning", "fa_plan_autotune", "fa_plan_tuning"]
 FA_COARSE_EULER, FA_COARSE_LEARNED = 0, 1
@@ -59,7 +59,8 @@ class fa_report(ctypes.Structure):
                 ("t_coarse_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double),
                 ("dx_history", ctypes.POINTER(ctypes.c_double)), ("g_fallback_iter", ctypes.c_int),
                 ("coef_fallbacks", ctypes.c_int), ("records", ctypes.c_int),
-                ("basis_dim", ctypes.c_int), ("fine_blocks", ctypes.c_int)]
+                ("basis_dim", ctypes.c_int), ("double_angle_steps", ctypes.c_int),
+                ("fine_blocks", ctypes.c_int)]
 
 
 class FaError(RuntimeError):
@@ -116,6 +117,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                         ctypes.c_float, ctypes.c_float, vp],
         "fa_batch_autotune": [vp, ctypes.POINTER(vp), ctypes.c_char_p],
         "fa_plan_autotune": [vp],
+        "fa_aima_plan": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(sz)],
+        "fa_aima": [vp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp,
+                    ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -479,6 +483,48 @@ class Plan:
             pass
 
 
+class Aima:
+    """Algorithm 8 (accelerated inverse-matrix approximation) through fa_aima_plan / fa_aima, with
+    a PyTorch-allocated workspace on the current CUDA stream."""
+
+    def __init__(self, n, dtype="f64", stream=None):
+        import torch
+
+        self.torch = torch
+        self.n = n
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        nb = ctypes.c_size_t()
+        _check(load_library().fa_aima_plan(ctypes.byref(h), n,
+                                           DTYPES[dtype] if isinstance(dtype, str) else int(dtype),
+                                           ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(nb)))
+        self.handle = h
+        self.ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device="cuda")
+        fa_plan_bind_workspace(self.handle, self.ws.data_ptr(), nb.value)
+
+    def run(self, A, X0, E, dt, steps):
+        """Returns (X^(steps), [||I - A X^(k)||_F for k = 0..steps])."""
+        t = lambda x: self.torch.as_tensor(x, dtype=self.torch.float64).cuda().contiguous()
+        A, X0, E = t(A), t(X0), t(E)
+        X = self.torch.empty_like(A)
+        res = (ctypes.c_double * (steps + 1))()
+        _check(load_library().fa_aima(self.handle, _ptr(A), _ptr(X0), _ptr(E), float(dt), steps,
+                                      _ptr(X), res))
+        return X, list(res)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Mlp:
     """The coefficient network's kernels on one parameter blob (training state on the device)."""
 
@@ -571,4 +617,5 @@ def _report(rep: fa_report, hist, status) -> dict:
             "t_fine_ms": rep.t_fine_ms, "t_coarse_ms": rep.t_coarse_ms,
             "t_refine_ms": rep.t_refine_ms, "status": status,
             "g_fallback_iter": rep.g_fallback_iter, "coef_fallbacks": rep.coef_fallbacks,
-            "records": rep.records, "basis_dim": rep.basis_dim, "fine_blocks": rep.fine_blocks}
+            "records": rep.records, "basis_dim": rep.basis_dim, "fine_blocks": rep.fine_blocks,
+            "double_angle_steps": rep.double_angle_steps}

@@ -37,10 +37,12 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("field,value", [("n", 0), ("N", 0), ("fine_steps", 0), ("coarse_steps", 0),
-                                         ("T", 0.0), ("T", -1.0), ("max_iters", -1), ("flow", 3),
+                                         ("T", 0.0), ("T", -1.0), ("max_iters", -1), ("flow", -1),
                                          ("fine_dtype", 9), ("coarse_dtype", 2), ("tol", -1.0),
                                          ("n", 20000), ("refine_steps", -2),
-                                         ("coarse_kind", 2), ("coarse_kind", -1)])
+                                         ("coarse_kind", 2), ("coarse_kind", -1), ("flow", 4),
+                                         ("method", 2), ("fine_scheme", 4), ("coarse_scheme", 4),
+                                         ("coarse_scheme", -1)])
 def test_plan_rejects_bad_descriptors(lib, field, value):
     d = fa.fa_problem_desc(n=8, flow=0, T=1.0, N=2, coarse_steps=1, fine_steps=2, max_iters=2,
                            tol=0.0, fine_dtype=fa.FA_BF16X4, coarse_dtype=fa.FA_BF16X4,
