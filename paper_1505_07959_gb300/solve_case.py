@@ -51,6 +51,9 @@ def main() -> None:
     ap.add_argument("--weights", default=learned.DEFAULT_WEIGHTS)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--repeats", type=int, default=1)
+    ap.add_argument("--method", default="classical", choices=["classical", "modified"],
+                    help="Algorithm 1, or the modified parareal of Section 3 (exp flow)")
+    ap.add_argument("--max-basis", type=int, default=0, help="modified: capacity of the space")
     args = ap.parse_args()
 
     import torch
@@ -63,7 +66,9 @@ def main() -> None:
     kind_c = fa.FA_COARSE_EULER if args.coarse == "euler" else fa.FA_COARSE_LEARNED
     plan = fa.Plan(args.n, flow, args.T, args.N, args.J, coarse_steps=args.m,
                    fine_dtype=args.dtype, coarse_dtype=args.coarse_dtype, max_iters=args.iters,
-                   tol=args.tol, refine_steps=args.refine, coarse_kind=kind_c)
+                   tol=args.tol, refine_steps=args.refine, coarse_kind=kind_c,
+                   method=fa.FA_METHOD_MODIFIED if args.method == "modified"
+                   else fa.FA_METHOD_CLASSICAL, max_basis=args.max_basis)
     if args.coarse == "taylor4":
         plan.set_learned(learned.constant_blob((1.0, 1.0, 1.0, 1.0)))
     elif args.coarse == "learned":
@@ -83,7 +88,8 @@ def main() -> None:
                "dx_history": ["%.3e" % d for d in rep["dx_history"]],
                "solve_ms": e0.elapsed_time(e1), "t_init_ms": rep["t_init_ms"],
                "t_fine_ms": rep["t_fine_ms"], "t_coarse_ms": rep["t_coarse_ms"],
-               "t_refine_ms": rep["t_refine_ms"], "rel_err": err}
+               "t_refine_ms": rep["t_refine_ms"], "rel_err": err, "method": args.method,
+               "basis_dim": rep["basis_dim"], "fine_blocks": rep["fine_blocks"]}
         print(json.dumps(out), flush=True)
     plan.close()
 
