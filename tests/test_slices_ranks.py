@@ -102,3 +102,47 @@ def test_bounds_cover_the_slices_once():
             assert spans[0][0] == 0 and spans[-1][1] == N
             assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
             assert max(h - l for l, h in spans) - min(h - l for l, h in spans) <= 1
+
+
+def _failing_rank_main(rank, ws, port, q):
+    """Rank 1's fine propagator raises on the second iteration (a host-side fault); rank 0 must
+    learn of it through the process group's timeout on its next collective, not hang."""
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=5))
+    flow, T, m, J = CASES["exp"]
+    sm = inputs.sym_matrix(6, "exp", 5)
+    N = 4
+    lo, hi = slices.bounds(N, ws, rank)
+    fine, coarse = oracle_propagators(sm.A, flow, T, N, m, J, hi - lo)
+    calls = {"n": 0}
+
+    def faulty_fine(U):
+        calls["n"] += 1
+        if rank == 1 and calls["n"] == 2:
+            raise RuntimeError("injected fault in the fine propagator")
+        return fine(U)
+
+    try:
+        slices.parareal_sliced(torch.eye(6, dtype=torch.float64), N, faulty_fine, coarse, N, 0.0,
+                               slices.TorchComm())
+        q.put((rank, "finished"))
+    except RuntimeError as e:
+        q.put((rank, "injected" if "injected" in str(e) else "peer-error"))
+    except Exception:
+        q.put((rank, "peer-error"))
+
+
+def test_a_failing_rank_is_detected_by_its_peers():
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in range(ws))
+    for p in procs:
+        p.join(60)
+    assert out[1] == "injected"
+    assert out[0] == "peer-error"           # the all-reduce (or receive) timed out with an error
