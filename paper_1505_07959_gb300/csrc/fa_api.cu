@@ -1391,37 +1391,50 @@ double host_sum(const double *h) {
 
 // globalQR step (Algorithm 2) for one block z against the basis Q_0 .. Q_{d-1}: two modified
 // Gram-Schmidt sweeps on a copy q, then r = ||q||_F; the block joins the basis as q / r when
-// r > drop ||z||_F and the space has room.  Returns through *kept.
+// r > drop ||z||_F and the space has room.  ||q|| is also read after the first sweep: the second
+// sweep removes only what rounding left along the basis and cannot lengthen q, so a block that
+// is already below the threshold is removed without it (the decision the full two sweeps would
+// take).  Returns through *kept.
 fa_status gs_extend(fa_plan_s *p, const double *z, int *d, bool *kept) {
   const size_t nn = p->nn;
+  const int dd = *d;
+  *kept = false;
+  if (dd >= p->cap) return FA_OK;                 // no room: the block is left to G
   double *q = p->Xout;
   double *pz = p->kpart, *pa = p->kpart + fa::kKrylovBlocks, *pb = pa + fa::kKrylovBlocks;
   FA_CUDA(cudaMemcpyAsync(q, z, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   FA_CUDA(fa::launch_gs_step(q, nullptr, nullptr, nullptr, nn, pz, p->stream));   // ||z||^2
-  const int dd = *d;
-  const double *prev = nullptr;
+  double hz[fa::kKrylovBlocks], hr[fa::kKrylovBlocks];
+  double zn = 0.0, r = 0.0;
   double *pin = pa, *pout = pb;
-  for (int pass = 0; pass < 2 && dd > 0; ++pass) {
-    for (int j = 0; j < dd; ++j) {
-      const double *next = p->Qb + static_cast<size_t>(j) * nn;
-      FA_CUDA(fa::launch_gs_step(q, prev, pin, next, nn, pout, p->stream));
-      prev = next;
+  auto read_norms = [&](const double *pr) -> fa_status {
+    FA_CUDA(cudaMemcpyAsync(hz, pz, sizeof(hz), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaMemcpyAsync(hr, pr, sizeof(hr), cudaMemcpyDeviceToHost, p->stream));
+    FA_CUDA(cudaStreamSynchronize(p->stream));
+    zn = std::sqrt(host_sum(hz));
+    r = std::sqrt(host_sum(hr));
+    if (!std::isfinite(zn) || !std::isfinite(r))
+      return set_err(FA_ERR_NONFINITE, "non-finite block in the parareal space");
+    return FA_OK;
+  };
+  if (dd == 0) {
+    FA_TRY(read_norms(pz));                       // the reduced block is z itself
+  } else {
+    for (int pass = 0; pass < 2; ++pass) {
+      const double *prev = nullptr;
+      for (int j = 0; j < dd; ++j) {
+        const double *next = p->Qb + static_cast<size_t>(j) * nn;
+        FA_CUDA(fa::launch_gs_step(q, prev, pin, next, nn, pout, p->stream));
+        prev = next;
+        std::swap(pin, pout);
+      }
+      FA_CUDA(fa::launch_gs_step(q, prev, pin, nullptr, nn, pout, p->stream));     // ||q||^2
       std::swap(pin, pout);
+      FA_TRY(read_norms(pin));
+      if (!(r > p->drop * zn && r > 0.0)) return FA_OK;   // removed
     }
   }
-  double *pr = pz;   // dd == 0: the reduced block is z itself
-  if (dd > 0) {
-    FA_CUDA(fa::launch_gs_step(q, prev, pin, nullptr, nn, pout, p->stream));       // ||q||^2
-    pr = pout;
-  }
-  double hz[fa::kKrylovBlocks], hr[fa::kKrylovBlocks];
-  FA_CUDA(cudaMemcpyAsync(hz, pz, sizeof(hz), cudaMemcpyDeviceToHost, p->stream));
-  FA_CUDA(cudaMemcpyAsync(hr, pr, sizeof(hr), cudaMemcpyDeviceToHost, p->stream));
-  FA_CUDA(cudaStreamSynchronize(p->stream));
-  const double zn = std::sqrt(host_sum(hz)), r = std::sqrt(host_sum(hr));
-  if (!std::isfinite(zn) || !std::isfinite(r))
-    return set_err(FA_ERR_NONFINITE, "non-finite block in the parareal space");
-  *kept = r > p->drop * zn && r > 0.0 && dd < p->cap;
+  *kept = r > p->drop * zn && r > 0.0;
   if (*kept) {
     FA_CUDA(fa::launch_scale_copy(q, 1.0 / r, nn, p->Qb + static_cast<size_t>(dd) * nn, p->stream));
     *d = dd + 1;
@@ -1951,6 +1964,7 @@ fa_status fa_parareal_solve(fa_plan_t p, const double *dA, const double *dX0, do
     if (dX0) return set_err(FA_ERR_ARG, "FA_FLOW_COS starts from (0; I): dX0 must be NULL");
     return cos_solve(p, dA, dXout, r);
   }
+  if (p->aima) return set_err(FA_ERR_ARG, "AIMA plans are run with fa_aima");
   if (p->d.refine_steps > 0 && p->d.flow == FA_FLOW_EXP)
     return set_err(FA_ERR_UNSUPPORTED, "the exponential flow has no refinement");
   const fa_problem_desc &d = p->d;
@@ -2094,6 +2108,8 @@ fa_status fa_parareal_solve_host(fa_plan_t p, const double *hA, const double *hX
                                  fa_report *r) {
   FA_TRY(check_ready(p, false));
   if (!hA || !hXout) return set_err(FA_ERR_ARG, "null pointer");
+  if (p->inner && hX0) return set_err(FA_ERR_ARG, "FA_FLOW_COS starts from (0; I): hX0 must be NULL");
+  if (p->aima) return set_err(FA_ERR_ARG, "AIMA plans are run with fa_aima");
   const size_t bytes = p->nn * sizeof(double);
   FA_CUDA(cudaMemcpyAsync(p->A64, hA, bytes, cudaMemcpyHostToDevice, p->stream));
   if (hX0) FA_CUDA(cudaMemcpyAsync(p->Xin, hX0, bytes, cudaMemcpyHostToDevice, p->stream));
