@@ -635,18 +635,49 @@ fa_status fine_sweep(fa_plan_s *p, const double *U, double *out, const double *g
 
 // ---- coarse sweep ----------------------------------------------------------------------------
 
+// Whether a tensor-core launch may compute the transposed product (X Y)^T = Y^T X^T with the
+// two operands' term buffers swapped (an L-form buffer read as the R form of the transpose, and
+// the other way round): the term pairs must be symmetric, so that the swapped launch forms the
+// same term products.
+bool transposable(const fa_plan_s *p) {
+  const fa::PairSet &s = p->ps;
+  if (s.terms_l != s.terms_r) return false;
+  for (int k = 0; k < s.npairs; ++k) {
+    bool found = false;
+    for (int q = 0; q < s.npairs; ++q) found = found || (s.a[q] == s.b[k] && s.b[q] == s.a[k]);
+    if (!found) return false;
+  }
+  return true;
+}
+
 // The product(s) of one forward-Euler substep on the single-slice coarse state vin (operand
-// terms in Vl/Vr[cur] when the coarse arithmetic is mixed), with the Euler epilogue e.
+// terms in Vl/Vr[cur] when the coarse arithmetic is mixed), with the Euler epilogue e.  Where
+// the pair set allows, the Euler launch computes the transposed product ((A V)^T = V^T A^T;
+// (V P)^T = P^T V^T; (V V)^T = V^T V^T), whose epilogue reaches the row-major float64 state with
+// coalesced accesses.
 fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
   const fa_problem_desc &d = p->d;
   const int tr = p->ps.terms_r;
   if (p->cmixed) {
     e.a_hi = p->a_hi;
     e.a_lo = p->a_lo;
+    const bool tp = transposable(p);
     if (d.flow == FA_FLOW_EXP) {
-      FA_TRY(tc(p, p->coarse_tmA(), p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+      if (tp) {
+        e.transposed = 1;
+        FA_TRY(tc(p, p->tmVr[cur], p->coarse_tmA(), tc_params(p, 1, 0, 0, e)));
+      } else {
+        FA_TRY(tc(p, p->coarse_tmA(), p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+      }
     } else if (d.flow == FA_FLOW_SQRT) {
-      FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+      if (tp) {
+        // (V V)^T = V^T V^T; K = A - P takes A's entries from the row-major float64 copy
+        e.transposed = 1;
+        e.a64 = p->A64;
+        FA_TRY(tc(p, p->tmVr[cur], p->tmVl[cur], tc_params(p, 1, 0, 0, e)));
+      } else {
+        FA_TRY(tc(p, p->tmVl[cur], p->tmVr[cur], tc_params(p, 1, 0, 0, e)));
+      }
     } else {
       EpiParams e1 = base_epi(p);
       e1.mode = fa::EPI_PROD;
@@ -654,7 +685,12 @@ fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
       e1.terms_r = tr;
       e1.term_stride_r = p->strideV;
       FA_TRY(tc(p, p->tmA, p->tmVr[cur], tc_params(p, 1, 0, 0, e1)));
-      FA_TRY(tc(p, p->tmVl[cur], p->tmPcr, tc_params(p, 1, 0, 0, e)));
+      if (tp) {
+        e.transposed = 1;
+        FA_TRY(tc(p, p->tmPcr, p->tmVl[cur], tc_params(p, 1, 0, 0, e)));
+      } else {
+        FA_TRY(tc(p, p->tmVl[cur], p->tmPcr, tc_params(p, 1, 0, 0, e)));
+      }
     }
   } else {
     e.a64 = p->A64;
@@ -673,10 +709,14 @@ fa_status euler_gemm(fa_plan_s *p, int cur, const double *vin, EpiParams e) {
   return FA_OK;
 }
 
-// BF16 operand terms of a single-slice coarse state into Vl/Vr[k].
+// BF16 operand terms of a single-slice coarse state into Vl/Vr[k], split from the float32
+// rounding as the Euler epilogue splits the states it writes: a sweep that starts from a state
+// (Step 0, or a slice range's first state received from elsewhere) computes the same bits as one
+// that reached it.
 fa_status split_coarse(fa_plan_s *p, const double *v, int k) {
   FA_CUDA(fa::launch_split_terms(v, 1, p->d.n, p->ldp, p->Vl[k], p->needs_l() ? p->ps.terms_l : 0,
-                                 p->strideV, p->Vr[k], p->ps.terms_r, p->strideV, 0, p->stream));
+                                 p->strideV, p->Vr[k], p->ps.terms_r, p->strideV,
+                                 fa::SPLIT_FROM_F32, p->stream));
   return FA_OK;
 }
 
@@ -1302,10 +1342,20 @@ void build_tables(fa_batch_s *b, std::vector<fa::TcSegment> &host) {
             e.terms_l = p->needs_l() ? p->ps.terms_l : 0;
             e.term_stride_r = e.term_stride_l = p->strideV;
             e.err = b->d_err;
-            if (d.flow == FA_FLOW_EXP)
+            // the same launches as the single-problem sweep (euler_gemm), transposed alike
+            const bool tp = transposable(p);
+            e.transposed = tp ? 1 : 0;
+            if (tp && d.flow == FA_FLOW_SQRT) e.a64 = p->A64;
+            if (d.flow == FA_FLOW_EXP && tp)
+              push_segment(host, t, p, p->tmVr[cur], p->tmA, 1, 0, 0, e);
+            else if (d.flow == FA_FLOW_EXP)
               push_segment(host, t, p, p->tmA, p->tmVr[cur], 1, 0, 0, e);
+            else if (d.flow == FA_FLOW_SQRT && tp)
+              push_segment(host, t, p, p->tmVr[cur], p->tmVl[cur], 1, 0, 0, e);
             else if (d.flow == FA_FLOW_SQRT)
               push_segment(host, t, p, p->tmVl[cur], p->tmVr[cur], 1, 0, 0, e);
+            else if (tp)
+              push_segment(host, t, p, p->tmPcr, p->tmVl[cur], 1, 0, 0, e);
             else
               push_segment(host, t, p, p->tmVl[cur], p->tmPcr, 1, 0, 0, e);
           }
@@ -1352,7 +1402,7 @@ fa_status batch_coarse(fa_batch_s *b, int mode) {
     fa_plan_s *p = b->plans[i];
     FA_CUDA(fa::launch_split_terms(p->U, 1, p->d.n, p->ldp, p->Vl[0],
                                    p->needs_l() ? p->ps.terms_l : 0, p->strideV, p->Vr[0],
-                                   p->ps.terms_r, p->strideV, 0, b->stream));
+                                   p->ps.terms_r, p->strideV, fa::SPLIT_FROM_F32, b->stream));
   }
   for (int n = 0; n < b->N; ++n)
     for (int sub = 0; sub < b->max_m; ++sub)
@@ -1821,8 +1871,8 @@ fa_status fa_aima(fa_plan_t p, const double *dA, const double *dX0, const double
   FA_CUDA(cudaMemcpyAsync(S[0] + nn, dE, nn * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
   const int tr = p->ps.terms_r;
   if (p->mixed)
-    FA_CUDA(fa::launch_split_terms(S[0], 2, n, p->ldp, nullptr, 0, 0, p->Yr[0], tr, p->strideY, 0,
-                                   p->stream));
+    FA_CUDA(fa::launch_split_terms(S[0], 2, n, p->ldp, nullptr, 0, 0, p->Yr[0], tr, p->strideY,
+                                   fa::SPLIT_FROM_F32, p->stream));
   int cur = 0;
   for (int k = 0; k <= steps; ++k) {
     EpiParams e = base_epi(p);
@@ -1836,7 +1886,13 @@ fa_status fa_aima(fa_plan_t p, const double *dA, const double *dX0, const double
       e.out_r = p->Yr[cur ^ 1];
       e.terms_r = tr;
       e.term_stride_r = p->strideY;
-      FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, 2, 0, 1, e)));
+      if (transposable(p)) {
+        // (A Y)^T = Y^T A^T: coalesced float64 state accesses in the epilogue
+        e.transposed = 1;
+        FA_TRY(tc(p, p->tmYr[cur], p->tmA, tc_params(p, 2, 1, 0, e)));
+      } else {
+        FA_TRY(tc(p, p->tmA, p->tmYr[cur], tc_params(p, 2, 0, 1, e)));
+      }
     } else {
       FA_TRY(f64(p, p->A64, 0, S[cur], nn, 2, e));
     }

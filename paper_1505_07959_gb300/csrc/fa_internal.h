@@ -91,6 +91,10 @@ struct EpiParams {
   int *err;                     // device error word
   int euler_step;               // EPI_STAGE with stage 4: an explicit step X <- X + h K (the
                                 // explicit-Euler and Crank-Nicolson fine schemes), no acc read
+  int transposed;               // EPI_EULER, EPI_AIMA: the launch computes the transposed
+                                // product (tile element (i, j) is entry (j, i) of the method's
+                                // product), so that a thread's float64 accesses to the
+                                // row-major state run along a row, coalesced across the warp
 };
 
 // One problem of a ragged (multi-problem) tensor-core launch: its tensor maps, epilogue
@@ -170,11 +174,14 @@ cudaError_t launch_tc_gemm_ragged(const TcSegment *segs, int nseg, int num_tiles
 int f64_tile(int n, int nb);
 int f64_tiles_per_slice(int n, int nb);
 
-// float64 row-major [nb][n][n] -> BF16 terms (L form and/or R form).  `ident`
-// adds -1 to the diagonal first and negates (to build I - A), when set.
+// float64 row-major [nb][n][n] -> BF16 terms (L form and/or R form).  Flags: SPLIT_I_MINUS
+// forms I - x first (to build I - A); SPLIT_FROM_F32 splits x rounded to float32, as the
+// epilogues split the states they write (so a state re-split on the host side gets the same
+// bits as the one an epilogue wrote); otherwise the split is taken from the float64 value.
+constexpr int SPLIT_I_MINUS = 1, SPLIT_FROM_F32 = 2;
 cudaError_t launch_split_terms(const double *src, int nb, int n, int ldp, __nv_bfloat16 *out_l,
                                int terms_l, size_t stride_l, __nv_bfloat16 *out_r, int terms_r,
-                               size_t stride_r, int i_minus, cudaStream_t s);
+                               size_t stride_r, int flags, cudaStream_t s);
 // float64 row-major [nb][n][n] -> column-major float32 hi/lo pair, plus BF16 terms
 // of hi (the first RK4 stage operand).
 cudaError_t launch_load_state(const double *U, int nb, int n, int ldp, float *x_hi, float *x_lo,

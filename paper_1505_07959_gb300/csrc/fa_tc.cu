@@ -127,22 +127,35 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
          (static_cast<uint32_t>(__bfloat16_as_ushort(b)) << 16);
 }
 
-// L form of 8 consecutive columns (one 16-byte store per term).
-__device__ __forceinline__ void put_l8(const EpiParams &e, size_t off, const Terms3 (&t)[8]) {
+// Terms of 8 consecutive elements at out + off (one 16-byte store per term).
+__device__ __forceinline__ void put8(__nv_bfloat16 *out, size_t stride, int terms, size_t off,
+                                     const Terms3 (&t)[8]) {
   uint4 w;
   w.x = pack2(t[0].t0, t[1].t0); w.y = pack2(t[2].t0, t[3].t0);
   w.z = pack2(t[4].t0, t[5].t0); w.w = pack2(t[6].t0, t[7].t0);
-  *reinterpret_cast<uint4 *>(e.out_l + off) = w;
-  if (e.terms_l > 1) {
+  *reinterpret_cast<uint4 *>(out + off) = w;
+  if (terms > 1) {
     w.x = pack2(t[0].t1, t[1].t1); w.y = pack2(t[2].t1, t[3].t1);
     w.z = pack2(t[4].t1, t[5].t1); w.w = pack2(t[6].t1, t[7].t1);
-    *reinterpret_cast<uint4 *>(e.out_l + e.term_stride_l + off) = w;
+    *reinterpret_cast<uint4 *>(out + stride + off) = w;
   }
-  if (e.terms_l > 2) {
+  if (terms > 2) {
     w.x = pack2(t[0].t2, t[1].t2); w.y = pack2(t[2].t2, t[3].t2);
     w.z = pack2(t[4].t2, t[5].t2); w.w = pack2(t[6].t2, t[7].t2);
-    *reinterpret_cast<uint4 *>(e.out_l + 2 * e.term_stride_l + off) = w;
+    *reinterpret_cast<uint4 *>(out + 2 * stride + off) = w;
   }
+}
+
+// L form of 8 consecutive columns.
+__device__ __forceinline__ void put_l8(const EpiParams &e, size_t off, const Terms3 (&t)[8]) {
+  put8(e.out_l, e.term_stride_l, e.terms_l, off, t);
+}
+
+__device__ __forceinline__ void put1(__nv_bfloat16 *out, size_t stride, int terms, size_t off,
+                                     const Terms3 &t) {
+  out[off] = t.t0;
+  if (terms > 1) out[stride + off] = t.t1;
+  if (terms > 2) out[2 * stride + off] = t.t2;
 }
 
 __device__ __forceinline__ void put_l1(const EpiParams &e, size_t off, const Terms3 &t) {
@@ -306,60 +319,212 @@ __device__ __forceinline__ void aima_chunk(const EpiParams &e, int b, int i, int
   }
 }
 
+// aima_chunk for a transposed launch (L = the state's R-form terms, R = A's row-major terms):
+// v[jj] is entry (j0 + jj, i) of A X or A u, so the thread updates column i of rows j0.. of the
+// row-major state, coalesced across the warp, and writes the next operand's R form (entry
+// (j, i) at i ldp + j) with one 16-byte store per term for 8 rows.  The residual terms are summed
+// in float32 per chunk and the terms split from the float32 value, as in the Euler epilogue.
+template <bool XS>   // XS: slice 0 (the iterate X), else slice 1 (the control u)
+__device__ __forceinline__ void aima_chunk_t(const EpiParams &e, int i, int j0, int cnt,
+                                             const float (&v)[32], double &s0) {
+  const int n = e.n;
+  const size_t nn = static_cast<size_t>(n) * n;
+  const bool fin = e.last != 0;
+  const double *__restrict__ xin = e.x64 + (XS ? 0 : nn);
+  const double *__restrict__ uin = e.x64 + nn;
+  double *__restrict__ out = e.out64 + (XS ? 0 : nn);
+  float f0 = 0.0f;
+#pragma unroll
+  for (int h8 = 0; h8 < 4; ++h8) {
+    const int gcnt = cnt - 8 * h8;
+    if (gcnt <= 0) break;
+    const size_t c0 = static_cast<size_t>(j0 + 8 * h8) * n + i;
+    if (fin) {
+      if (XS) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const double res = (i == j0 + 8 * h8 + u ? 1.0 : 0.0) - static_cast<double>(v[8 * h8 + u]);
+          const float rf = u < gcnt ? static_cast<float>(res) : 0.0f;
+          f0 = fmaf(rf, rf, f0);
+        }
+      }
+      continue;
+    }
+    double y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) y[u] = u < gcnt ? xin[c0 + static_cast<size_t>(u) * n] : 0.0;
+    if (XS) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const double w = u < gcnt ? uin[c0 + static_cast<size_t>(u) * n] : 0.0;
+        const double res = (i == j0 + 8 * h8 + u ? 1.0 : 0.0) - static_cast<double>(v[8 * h8 + u]);
+        const float rf = u < gcnt ? static_cast<float>(res) : 0.0f;
+        f0 = fmaf(rf, rf, f0);
+        y[u] += e.dt * (res + w);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) y[u] -= e.dt * static_cast<double>(v[8 * h8 + u]);
+    }
+    Terms3 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u < gcnt) out[c0 + static_cast<size_t>(u) * n] = y[u];
+      t[u] = split3_f32(static_cast<float>(y[u]));
+    }
+    if (e.terms_r) {
+      const size_t off = (static_cast<size_t>(XS ? 0 : 1) * n + i) * e.ldp + j0 + 8 * h8;
+      if (gcnt >= 8) {
+        put8(e.out_r, e.term_stride_r, e.terms_r, off, t);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < gcnt) put1(e.out_r, e.term_stride_r, e.terms_r, off + u, t[u]);
+      }
+    }
+  }
+  s0 += static_cast<double>(f0);
+}
+
 // Forward-Euler substep G = V + dt Fl(V) on 32 columns of row i (single slice,
 // row-major float64); on the last substep also G_n, the correction
-// V_{n+1} = G_n + D_n and the norm terms.  Writes V's operand terms.
+// V_{n+1} = G_n + D_n and the norm terms.  Writes V's operand terms.  Columns go in groups of
+// 8 whose float64 loads are issued before any of them is used.  The norm terms of the chunk are
+// summed in float32 (relative accuracy ~1e-6, ample for the stopping test) and V's BF16 terms
+// are split from V rounded to float32 (the 24 bits that three BF16 terms hold): float64
+// arithmetic runs on the GPU's slowest pipe and bounds this epilogue.
 __device__ __forceinline__ void euler_chunk(const EpiParams &e, int i, int j0, int cnt,
                                             const float (&v)[32], double &s0, double &s1) {
   const int n = e.n;
   const size_t r0 = static_cast<size_t>(i) * n + j0;
-  double Vn[32];
+  const bool last = e.euler_last != 0;
+  const bool sq = e.flow == FA_FLOW_SQRT;
+  float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
-  for (int jj = 0; jj < 32; ++jj) {
-    Vn[jj] = 0.0;
-    if (jj < cnt) {
+  for (int h8 = 0; h8 < 4; ++h8) {
+    const int gcnt = cnt - 8 * h8;
+    if (gcnt <= 0) break;
+    double vi[8], di[8], uo[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool ok = u < gcnt;
+      const size_t c = r0 + 8 * h8 + u;
+      vi[u] = ok ? e.v_in[c] : 0.0;
+      di[u] = (ok && last && e.d_in) ? e.d_in[c] : 0.0;
+      uo[u] = (ok && last && e.u_old) ? e.u_old[c] : 0.0;
+    }
+    Terms3 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int jj = 8 * h8 + u;
       double K = static_cast<double>(v[jj]);
-      if (e.flow == FA_FLOW_SQRT) {
+      if (sq && u < gcnt) {
         const size_t ca = static_cast<size_t>(j0 + jj) * n + i;
         K = (static_cast<double>(e.a_hi[ca]) + static_cast<double>(e.a_lo[ca])) - K;
       }
-      const double G = e.v_in[r0 + jj] + e.dt * K;
+      const double G = vi[u] + e.dt * K;
       double V = G;
-      if (e.euler_last) {
-        e.g_out[r0 + jj] = G;
-        if (e.d_in) V = G + e.d_in[r0 + jj];
-        if (e.u_old) {
-          const double dl = V - e.u_old[r0 + jj];
-          s0 += dl * dl;
-          s1 += V * V;
+      if (u < gcnt) {
+        if (last) {
+          e.g_out[r0 + jj] = G;
+          V = G + di[u];
         }
+        e.v_out[r0 + jj] = V;
       }
-      e.v_out[r0 + jj] = V;
-      Vn[jj] = V;
+      const float vf = static_cast<float>(V);
+      if (last && e.u_old && u < gcnt) {
+        const float dl = static_cast<float>(V - uo[u]);
+        f0 = fmaf(dl, dl, f0);
+        f1 = fmaf(vf, vf, f1);
+      }
+      t[u] = split3_f32(vf);
     }
-  }
-  if (!e.terms_r && !e.terms_l) return;
-#pragma unroll
-  for (int h8 = 0; h8 < 4; ++h8) {
-    Terms3 t[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] = split3_f64(Vn[8 * h8 + u]);
     if (e.terms_r) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (8 * h8 + u < cnt) put_r(e, 0, i, j0 + 8 * h8 + u, t[u]);
+        if (u < gcnt) put_r(e, 0, i, j0 + 8 * h8 + u, t[u]);
     }
     if (e.terms_l) {
       const size_t off = static_cast<size_t>(i) * e.ldp + j0 + 8 * h8;
-      if (8 * h8 + 8 <= cnt) {
+      if (gcnt >= 8) {
         put_l8(e, off, t);
       } else {
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (8 * h8 + u < cnt) put_l1(e, off + u, t[u]);
+          if (u < gcnt) put_l1(e, off + u, t[u]);
       }
     }
   }
+  s0 += static_cast<double>(f0);
+  s1 += static_cast<double>(f1);
+}
+
+// euler_chunk for a transposed launch: v[jj] is entry (j0 + jj, i) of the product, so the
+// thread updates column i of rows j0.. of the row-major state (consecutive lanes, consecutive
+// addresses); the square-root flow's K = A - P takes A from its row-major float64 copy.  V's R form (entry (j, i) at i ldp + j) takes one 16-byte store per term for 8
+// rows; its L form (at j ldp + i) is coalesced across the warp.
+__device__ __forceinline__ void euler_chunk_t(const EpiParams &e, int i, int j0, int cnt,
+                                              const float (&v)[32], double &s0, double &s1) {
+  const int n = e.n;
+  const bool last = e.euler_last != 0;
+  const bool sq = e.flow == FA_FLOW_SQRT;   // K = A - V V: entry (j, i) of A, row-major float64
+  float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+  for (int h8 = 0; h8 < 4; ++h8) {
+    const int gcnt = cnt - 8 * h8;
+    if (gcnt <= 0) break;
+    double vi[8], di[8], uo[8], am[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool ok = u < gcnt;
+      const size_t c = static_cast<size_t>(j0 + 8 * h8 + u) * n + i;
+      vi[u] = ok ? e.v_in[c] : 0.0;
+      di[u] = (ok && last && e.d_in) ? e.d_in[c] : 0.0;
+      uo[u] = (ok && last && e.u_old) ? e.u_old[c] : 0.0;
+      am[u] = (ok && sq) ? e.a64[c] : 0.0;
+    }
+    Terms3 t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const size_t c = static_cast<size_t>(j0 + 8 * h8 + u) * n + i;
+      const double P = static_cast<double>(v[8 * h8 + u]);
+      const double G = vi[u] + e.dt * (sq ? am[u] - P : P);
+      double V = G;
+      if (u < gcnt) {
+        if (last) {
+          e.g_out[c] = G;
+          V = G + di[u];
+        }
+        e.v_out[c] = V;
+      }
+      const float vf = static_cast<float>(V);
+      if (last && e.u_old && u < gcnt) {
+        const float dl = static_cast<float>(V - uo[u]);
+        f0 = fmaf(dl, dl, f0);
+        f1 = fmaf(vf, vf, f1);
+      }
+      t[u] = split3_f32(vf);
+    }
+    if (e.terms_r) {
+      const size_t off = static_cast<size_t>(i) * e.ldp + j0 + 8 * h8;
+      if (gcnt >= 8) {
+        put8(e.out_r, e.term_stride_r, e.terms_r, off, t);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < gcnt) put1(e.out_r, e.term_stride_r, e.terms_r, off + u, t[u]);
+      }
+    }
+    if (e.terms_l) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < gcnt)
+          put1(e.out_l, e.term_stride_l, e.terms_l,
+               static_cast<size_t>(j0 + 8 * h8 + u) * e.ldp + i, t[u]);
+    }
+  }
+  s0 += static_cast<double>(f0);
+  s1 += static_cast<double>(f1);
 }
 
 // Operand terms (L form and/or R form) of 32 float values of row i, columns j0.. of slice b.
@@ -411,13 +576,22 @@ __device__ __forceinline__ void store_chunk(const EpiParams &e, int b, int i, in
   const size_t r0 = static_cast<size_t>(b) * n * n + static_cast<size_t>(i) * n + j0;
   float w[32];
 #pragma unroll
-  for (int jj = 0; jj < 32; ++jj) {
-    double val = e.alpha * static_cast<double>(v[jj]) + (i == j0 + jj ? e.beta : 0.0);
-    if (jj < cnt) {
-      if (e.store_add) val += e.store_add[r0 + jj];
-      if (e.store_out) e.store_out[r0 + jj] = val;
+  for (int h8 = 0; h8 < 4; ++h8) {
+    // the group's addend loads go out before its stores (which may alias them)
+    double ad[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      ad[u] = (e.store_add && 8 * h8 + u < cnt) ? e.store_add[r0 + 8 * h8 + u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int jj = 8 * h8 + u;
+      double val = e.alpha * static_cast<double>(v[jj]) + (i == j0 + jj ? e.beta : 0.0);
+      if (jj < cnt) {
+        if (e.store_add) val += ad[u];
+        if (e.store_out) e.store_out[r0 + jj] = val;
+      }
+      w[jj] = static_cast<float>(val);
     }
-    w[jj] = static_cast<float>(val);
   }
   if (e.terms_r || e.terms_l) write_terms(e, b, i, j0, cnt, w);
 }
@@ -478,6 +652,23 @@ __device__ __forceinline__ void prefetch_tile_state(const EpiParams &e, int b, i
         if (!arr[a]) continue;
         const float *c = arr[a] + (a < 3 ? b * nn : 0) + static_cast<size_t>(j) * n + i0;
         ptx::prefetch_l2(c);
+        ptx::prefetch_l2(c + last);
+      }
+    }
+  } else if (e.mode == EPI_EULER && e.transposed) {
+    // transposed launch: the warp's 32 rows are 32 consecutive columns of the row-major state
+    const int last = n - 1 - i0 < 31 ? n - 1 - i0 : 31;
+    const double *arr[4] = {e.v_in, e.d_in, e.u_old, e.flow == FA_FLOW_SQRT ? e.a64 : nullptr};
+#pragma unroll
+    for (int k = 0; k < BN / 32; ++k) {
+      const int j = ntile * BN + lane + 32 * k;
+      if (j >= n) break;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (!arr[a]) continue;
+        const double *c = arr[a] + static_cast<size_t>(j) * n + i0;   // <= 3 lines of 128 B
+        ptx::prefetch_l2(c);
+        ptx::prefetch_l2(c + (last < 16 ? last : 16));
         ptx::prefetch_l2(c + last);
       }
     }
@@ -966,16 +1157,22 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
           }
           }
+        } else if constexpr (FP8) {
+          // E4M3 launches are RK4 stages of the square-root fine sweep only: the other
+          // epilogues are not compiled into this instantiation
         } else if (e.mode == EPI_PROD) {
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj)
             if (jj < cnt) put_r(e, gb, i, j0 + jj, split3_f32(v[jj]));
         } else if (e.mode == EPI_EULER) {
-          euler_chunk(e, i, j0, cnt, v, s0, s1);
+          if (e.transposed) euler_chunk_t(e, i, j0, cnt, v, s0, s1);
+          else euler_chunk(e, i, j0, cnt, v, s0, s1);
         } else if (e.mode == EPI_TAYLOR) {
           taylor_chunk(e, gb, i, j0, cnt, v);
         } else if (e.mode == EPI_AIMA) {
-          aima_chunk(e, gb, i, j0, cnt, v, s0);
+          if (!e.transposed) aima_chunk(e, gb, i, j0, cnt, v, s0);
+          else if (gb == 0) aima_chunk_t<true>(e, i, j0, cnt, v, s0);
+          else aima_chunk_t<false>(e, i, j0, cnt, v, s0);
         } else {
           store_chunk(e, gb, i, j0, cnt, v);
         }
@@ -1049,22 +1246,24 @@ constexpr int TT = 32;
 __global__ void split_terms_kernel(const double *__restrict__ src, int n, int ldp,
                                    __nv_bfloat16 *out_l, int terms_l, size_t stride_l,
                                    __nv_bfloat16 *out_r, int terms_r, size_t stride_r,
-                                   int i_minus) {
+                                   int flags) {
   __shared__ double tile[TT][TT + 1];
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
   const size_t nn = static_cast<size_t>(n) * n;
   const double *S = src + b * nn;
   const int nt = terms_l > terms_r ? terms_l : terms_r;
+  const bool from_f32 = (flags & SPLIT_FROM_F32) != 0;
   for (int r = threadIdx.y; r < TT; r += blockDim.y) {
     const int i = i0 + r, j = j0 + threadIdx.x;
     double x = 0.0;
     if (i < n && j < n) {
       x = S[static_cast<size_t>(i) * n + j];
-      if (i_minus) x = (i == j ? 1.0 : 0.0) - x;
+      if (flags & SPLIT_I_MINUS) x = (i == j ? 1.0 : 0.0) - x;
       if (terms_l) {
         __nv_bfloat16 t[3];
-        split_f64(x, nt, t);
+        if (from_f32) split_f32(static_cast<float>(x), nt, t);
+        else split_f64(x, nt, t);
         const size_t off = (static_cast<size_t>(b) * n + i) * ldp + j;
         for (int k = 0; k < terms_l; ++k) out_l[k * stride_l + off] = t[k];
       }
@@ -1077,7 +1276,8 @@ __global__ void split_terms_kernel(const double *__restrict__ src, int n, int ld
     const int j = j0 + r, i = i0 + threadIdx.x;
     if (i < n && j < n) {
       __nv_bfloat16 t[3];
-      split_f64(tile[threadIdx.x][r], nt, t);
+      if (from_f32) split_f32(static_cast<float>(tile[threadIdx.x][r]), nt, t);
+      else split_f64(tile[threadIdx.x][r], nt, t);
       const size_t off = (static_cast<size_t>(b) * n + j) * ldp + i;
       for (int k = 0; k < terms_r; ++k) out_r[k * stride_r + off] = t[k];
     }
@@ -1301,10 +1501,10 @@ cudaError_t launch_fp8_load(const double *U, int nb, int n, int ldp8, uint8_t *o
 
 cudaError_t launch_split_terms(const double *src, int nb, int n, int ldp, __nv_bfloat16 *out_l,
                                int terms_l, size_t stride_l, __nv_bfloat16 *out_r, int terms_r,
-                               size_t stride_r, int i_minus, cudaStream_t s) {
+                               size_t stride_r, int flags, cudaStream_t s) {
   dim3 grid((n + TT - 1) / TT, (n + TT - 1) / TT, nb), block(TT, 8);
   split_terms_kernel<<<grid, block, 0, s>>>(src, n, ldp, out_l, terms_l, stride_l, out_r,
-                                            terms_r, stride_r, i_minus);
+                                            terms_r, stride_r, flags);
   count_launch();
   return cudaGetLastError();
 }
