@@ -66,11 +66,14 @@ def test_fine_sweep_mixed(dtype, n, flow, kind, T):
     assert max(errs) < SWEEP_TOL[dtype], errs
 
 
+@pytest.mark.parametrize("n", [96, 101])
 @pytest.mark.parametrize("m", [1, 3])
 @pytest.mark.parametrize("dtype", ["f64", "bf16x6"])
 @pytest.mark.parametrize("flow,kind,T", FLOWS)
-def test_coarse_sweep(m, dtype, flow, kind, T):
-    n, N = 96, 5
+def test_coarse_sweep(n, m, dtype, flow, kind, T):
+    """Step 0 and the corrected sweep with norms.  n = 101 leaves a 5-column tail in the last
+    32-column chunk (the epilogues' element-wise path) and padded operand rows (ldp = 104)."""
+    N = 5
     sm = inputs.sym_matrix(n, kind, 7)
     rng = np.random.default_rng(3)
     D = rng.standard_normal((N, n, n)) * 1e-3
@@ -101,3 +104,30 @@ def test_coarse_sweep(m, dtype, flow, kind, T):
         # which the difference V - Uold (~1e-2 of V) magnifies 100-fold in d2.
         assert abs(normsg[k, 0] - d2) <= (1e-10 if dtype == "f64" else 1e-4) * d2
         assert abs(normsg[k, 1] - v2) <= (1e-12 if dtype == "f64" else 1e-6) * v2
+
+
+@pytest.mark.parametrize("flow,kind,T", FLOWS)
+def test_coarse_sweep_bf16x4_row_epilogue(flow, kind, T):
+    """BF16x4's term pairs are not symmetric (three terms of the left factor, two of the right),
+    so its Euler launches keep the untransposed product and the row-per-thread epilogue: that
+    path against the oracle on a ragged size, Step 0 and the corrected sweep with norms."""
+    n, N, m = 101, 4, 1
+    sm = inputs.sym_matrix(n, kind, 8)
+    rng = np.random.default_rng(4)
+    D = rng.standard_normal((N, n, n)) * 1e-3
+    Uold = np.stack([np.eye(n)] + [np.eye(n) + 0.01 * rng.standard_normal((n, n)) for _ in range(N)])
+    plan = fa.Plan(n, flow, T, N, fine_steps=2, coarse_steps=m, fine_dtype="bf16x4")
+    plan.set_matrix(dev(sm.A))
+    Ug, Gg, normsg = plan.coarse_sweep(dev(np.eye(n)), D=dev(D), Uold=dev(Uold))
+    U1, G1 = orc.coarse_sweep(sm.A, flow, T, N, m, np.eye(n), list(D))
+    Ug, Gg, normsg = host(Ug), host(Gg), host(normsg)
+    plan.close()
+    # the BF16x4 product error (~4e-6 of the product, test_gpu_12) times dt ||Fl'|| per step
+    for k in range(N + 1):
+        assert rel(Ug[k], U1[k]) < 3e-5, k
+    for k in range(N):
+        assert rel(Gg[k], G1[k]) < 3e-5, k
+        d2 = orc.fro(U1[k + 1] - Uold[k + 1]) ** 2
+        v2 = orc.fro(U1[k + 1]) ** 2
+        assert abs(normsg[k, 0] - d2) <= 5e-3 * d2
+        assert abs(normsg[k, 1] - v2) <= 1e-4 * v2
