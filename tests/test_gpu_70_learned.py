@@ -456,3 +456,21 @@ def test_trained_weights_beat_euler_on_held_out_matrices():
     for k in res:
         for r in res[k]:
             assert r["converged"] and r["err"] < 1e-12 and r["g_fallback_iter"] == 0, (k, r)
+
+
+def test_trained_weights_at_the_top_of_the_training_range():
+    """The committed network at n = 1024 (the top of its training range), two held-out seeds,
+    N = 64, J = 64: fewer parareal iterations than forward Euler and no more than the Taylor-4
+    control on average, every result refined to float64 accuracy."""
+    cuda_or_fail()
+    from paper_1505_07959_gb300 import learned as LG
+    params = np.fromfile(LG.DEFAULT_WEIGHTS, dtype=np.float32)
+    res = LG.evaluate(params, ns=(1024,), seeds=range(200010, 200012), N=64, J=64, tol=1e-8,
+                      dtype="bf16x6", coarse_dtype="f64", refine_steps=2)
+    it = {k: np.mean([r["iters"] for r in res[k]]) for k in res}
+    print(f"learned G at n = 1024: mean iterations {it}")
+    assert it["learned"] < it["euler"], it
+    assert it["learned"] <= it["taylor4"], it
+    for k in res:
+        for r in res[k]:
+            assert r["converged"] and r["err"] < 1e-12, (k, r)
