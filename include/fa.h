@@ -40,7 +40,10 @@
  *   with fa_plan_bind_workspace (the library calls no cudaMalloc).
  * - Mixed-precision forms (FA_BF16*) use BF16 tensor-core products with
  *   float32 accumulation, a double-float32 (hi + lo) RK4 state, and float64
- *   for the parareal correction, the coarse-state additions and the norms.
+ *   for the parareal correction and the coarse-state additions; the norm
+ *   terms of the stopping test are summed in float32 over 32 columns of a row
+ *   and in float64 beyond (about 1e-6 relative, enough for any tolerance the
+ *   products can reach).
  */
 #ifndef FA_H
 #define FA_H
@@ -214,7 +217,8 @@ fa_status fa_fine_sweep(fa_plan_t p, const double *dU, double *dF);
  * the same array as dUnew, read before overwritten) must be given and
  * dNorms[2n], dNorms[2n+1] (float64, device, [N][2]) receive
  * ||V_{n+1} - Uold_{n+1}||_F^2 and ||V_{n+1}||_F^2, summed in a fixed order
- * (bitwise reproducible). */
+ * (bitwise reproducible; in the mixed forms each 32-column run of a row in
+ * float32, the rest in float64). */
 fa_status fa_coarse_sweep(fa_plan_t p, const double *dU0, const double *dD,
                           double *dUnew, double *dGnew, double *dNorms,
                           const double *dUold);
