@@ -4,7 +4,8 @@
 // with clock64.  It first checks that an A operand copied into TMEM with tcgen05.cp gives the
 // same product as A read from shared memory, then reports cycles per MMA for: 128x128 from
 // shared memory; A from TMEM; 128x256; 128x128 into two and four accumulators in turn; 128x64;
-// and 128x128 issued from two warps.  Every wait is bounded; a timeout is reported, not hung on.
+// and 128x128 issued from two warps (on the same tiles, and each on its own) and from two lanes
+// of one warp.  Every wait is bounded; a timeout is reported, not hung on.
 // Output: one line per form, "<form> grid <g>: <c> cycles per MMA (nominal <n>), ...".
 #include <cstdint>
 #include <cstdio>
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(128, 1) probe(int mode, int iters, const __nv_
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = sm;                 // 128 rows x 128 B
   uint8_t *sB = sm + 16384;         // 256 rows x 128 B
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 16384 + 32768);
+  uint8_t *sA2 = sm + 16384 + 32768;  // a copy of A at its own address (mode 9)
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 16384 + 32768 + 16384);
   uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
   const int t = threadIdx.x;
   // swizzled K-major fill: element (r, k), k < 64: byte r*128 + (((2k)/16) ^ (r%8))*16 + (2k)%16
@@ -73,6 +75,7 @@ __global__ void __launch_bounds__(128, 1) probe(int mode, int iters, const __nv_
     const int r = idx / 64, k = idx % 64;
     const int off = r * 128 + ((((2 * k) / 16) ^ (r % 8)) * 16) + (2 * k) % 16;
     *reinterpret_cast<__nv_bfloat16 *>(sA + off) = gA[idx];
+    *reinterpret_cast<__nv_bfloat16 *>(sA2 + off) = gA[idx];
   }
   for (int idx = t; idx < 256 * 64; idx += 128) {
     const int r = idx / 64, k = idx % 64;
@@ -101,18 +104,23 @@ __global__ void __launch_bounds__(128, 1) probe(int mode, int iters, const __nv_
   const uint32_t id = idesc(128, N);
   const uint32_t tA = base + 256;   // columns [256, 288): A's 4 K-steps x 8 columns
   bool ok = true;
-  if (mode == 7 && (t == 0 || t == 32)) {
-    // two issuing warps (lane 0 of warps 0 and 1), each its own N = 128 accumulator
-    const uint32_t d = base + (t == 32 ? 128u : 0u);
+  if (((mode == 7 || mode == 9) && (t == 0 || t == 32)) || (mode == 8 && (t == 0 || t == 1))) {
+    // two issuing threads, each its own N = 128 accumulator: lane 0 of warps 0 and 1 (mode 7,
+    // both on the same operand tiles; mode 9, each on its own two tiles) or lanes 0 and 1 of
+    // warp 0 (mode 8)
+    const bool second = mode == 8 ? t == 1 : t == 32;
+    const uint32_t d = base + (second ? 128u : 0u);
+    const uint64_t a = (mode == 9 && second) ? sdesc(su32(sA2)) : dA;
+    const uint64_t b = (mode == 9 && second) ? sdesc(su32(sB + 16384)) : dB;
     const long long c0 = clock64();
     for (int it = 0; it < iters; ++it)
       for (int kk = 0; kk < 4; ++kk)
-        mma_ss(d, dA + 2u * kk, dB + 2u * kk, idesc(128, 128), (it > 0 || kk > 0) ? 1u : 0u);
-    commit(bar + (t == 32 ? 1 : 0));
-    ok = wait(bar + (t == 32 ? 1 : 0), 0);
+        mma_ss(d, a + 2u * kk, b + 2u * kk, idesc(128, 128), (it > 0 || kk > 0) ? 1u : 0u);
+    commit(bar + (second ? 1 : 0));
+    ok = wait(bar + (second ? 1 : 0), 0);
     if (t == 0) cyc[blockIdx.x] = clock64() - c0;
     if (!ok) atomicExch(err, 1);
-  } else if (mode != 7 && t == 0) {
+  } else if (mode < 7 && t == 0) {
     if (mode == 1) {
       for (int kk = 0; kk < 4; ++kk) cp_128x256b(tA + 8 * kk, dA + 2u * kk);
       commit(bar + 1);
@@ -198,10 +206,11 @@ int main(int argc, char **argv) {
   }
   int same = 0; for (int i = 0; i < 128 * 128; ++i) same += (res[0][i] == res[1][i]);
   printf("TMEM-A vs smem-A: %d of %d elements bitwise equal\n", same, 128 * 128);
-  const char *names[8] = {"A,B smem N=128", "A tmem, B smem N=128", "A,B smem N=256",
-                          "N=128, 2 accumulators", "N=128, 4 accumulators", "N=256, 2 accumulators",
-                          "N=64", "N=128, 2 issuing warps"};
-  for (int mode = 0; mode < 8; ++mode) {
+  const char *names[10] = {"A,B smem N=128", "A tmem, B smem N=128", "A,B smem N=256",
+                           "N=128, 2 accumulators", "N=128, 4 accumulators", "N=256, 2 accumulators",
+                           "N=64", "N=128, 2 issuing warps", "N=128, 2 lanes of a warp",
+                           "N=128, 2 warps, own tiles"};
+  for (int mode = 0; mode < 10; ++mode) {
     const int iters = 2000;
     cudaMemset(dErr, 0, 4);
     probe<<<grid, 128, smem>>>(mode, iters, dA, dB, dOut, dCyc, dErr);
@@ -212,7 +221,7 @@ int main(int argc, char **argv) {
     cudaMemcpy(cyc.data(), dCyc, grid * 8, cudaMemcpyDeviceToHost);
     double avg = 0; for (auto c : cyc) avg += c; avg /= grid;
     const int N = (mode == 2 || mode == 5) ? 256 : (mode == 6 ? 64 : 128);
-    const double per = avg / (iters * 4.0 * (mode == 7 ? 2 : 1));
+    const double per = avg / (iters * 4.0 * (mode >= 7 ? 2 : 1));
     printf("%-22s grid %d: %.1f cycles per MMA (nominal %d), %.0f flop/cycle/SM\n", names[mode], grid,
            per, N / 2, 2.0 * 128 * N * 16 / per);
   }
