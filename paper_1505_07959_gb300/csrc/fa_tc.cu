@@ -20,7 +20,7 @@
 // where their per-tile scales are applied).
 //
 // Data movement.  Each k-block's operand term tiles (16 KB each) are loaded
-// once by TMA into a 13-slot shared-memory ring and every term pair that uses
+// once by TMA into a 12-slot shared-memory ring and every term pair that uses
 // them is issued from there, so about two k-blocks are in flight.
 //
 // Roles (one CTA per SM, 10 warps): warp 0 issues TMA loads; warp 1 issues
@@ -34,7 +34,14 @@
 // persistently, M-tile fastest.
 //
 // TMEM columns: [0,128) and [128,256) main-product chunks (double-buffered),
-// [256,384) correction accumulator, [384,512) finished tile.
+// [256,384) correction accumulator, [384,512) finished tile.  Six-pair launches: [0,128)
+// the one main chunk, [128,384) a 128x256 correction accumulator, [384,512) finished tile.
+//
+// Issue.  One thread issues one tcgen05.mma about every 117 cycles whatever N up to 128
+// (128x256: about 161), while the tensor core completes a 128x128x16 product in 64, so the
+// six-pair launches issue their five correction products as three: L0 [R1 | R2]^T and
+// L1 [R0 | R1]^T as 128x256 products over two adjacent R tiles, and L2 R0^T; the two halves
+// of the wide accumulator are summed when the tile is finished.
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -50,7 +57,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;
-constexpr int NSLOT = 13;
+constexpr int NSLOT = 12;                     // two six-tile k-blocks: a k-block's tiles never wrap
 constexpr int NKB = 8;                        // k-block release barriers (> k-blocks in flight)
 constexpr int TILE_BYTES = BM * BK * 2;       // one operand term tile: 128 rows x 64 BF16
 constexpr int STORE_WARPS = 4;                // one per TMEM lane quarter
@@ -59,6 +66,7 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t MB_COL0 = 0;               // main-product chunks: [0,128) and [128,256)
 constexpr uint32_t CB_COL = 256;
 constexpr uint32_t FIN_COL = 384;
+constexpr uint32_t WIDE_COL = 128;            // six pairs: the 128x256 correction accumulator
 constexpr size_t SMEM_BYTES = size_t(NSLOT) * TILE_BYTES + 1024 + 512;
 
 __device__ __forceinline__ void split_f32(float x, int nt, __nv_bfloat16 *t) {
@@ -787,6 +795,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
+  // Six-pair BF16 launches issue their correction products as 128x256 MMAs (see the MMA
+  // issuer) into TMEM columns [128, 384); their main chunk is single-buffered.
+  const bool wide = !FP8 && p.npairs == 6;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NKB; ++s) {
       ptx::mbar_init(full + s, 1);
@@ -909,7 +920,35 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           ptx::tc_fence_after();
-          if (ptx::elect_one()) {
+          if (wide) {
+            if (ptx::elect_one()) {
+              // the k-block's tiles sit in slots sb .. sb + 5 in the order L0 L1 L2 R0 R1 R2
+              const uint32_t sb = g % NSLOT;
+              const uint64_t dL0 = desc0 + static_cast<uint64_t>(sb * (TILE_BYTES >> 4));
+              const uint64_t step = TILE_BYTES >> 4;
+              const uint32_t dmain = tmem_base + MB_COL0;
+              const uint32_t dwide = tmem_base + WIDE_COL;
+              constexpr uint32_t idesc256 = ptx::idesc_bf16_f32(BM, 2 * BN);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)      // main: L0 R0^T, fresh per k-block
+                ptx::tc_mma_bf16(dmain, dL0 + 2u * kk, dL0 + 3 * step + 2u * kk, idesc,
+                                 kk > 0 ? 1u : 0u);
+              ptx::tc_commit(mbfull);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)      // L0 [R1 | R2]^T
+                ptx::tc_mma_bf16(dwide, dL0 + 2u * kk, dL0 + 4 * step + 2u * kk, idesc256,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)      // L1 [R0 | R1]^T
+                ptx::tc_mma_bf16(dwide, dL0 + step + 2u * kk, dL0 + 3 * step + 2u * kk, idesc256,
+                                 1u);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)      // L2 R0^T into the first half
+                ptx::tc_mma_bf16(dwide, dL0 + 2 * step + 2u * kk, dL0 + 3 * step + 2u * kk,
+                                 idesc, 1u);
+              ptx::tc_commit(kbempty + k % NKB);
+            }
+          } else if (ptx::elect_one()) {
             const uint32_t dmain = tmem_base + MB_COL0 + static_cast<uint32_t>(mb * BN);
             const uint32_t dcorr = tmem_base + CB_COL;
 #pragma unroll
@@ -936,7 +975,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           __syncwarp();
           g += ntl;
           if (close) {
-            mb ^= 1;
+            if (!wide) mb ^= 1;             // six pairs: one main chunk
             if (mb == 0) mph ^= 1u;
           }
         }
@@ -991,7 +1030,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (prof) atomicAdd(prof + 9, static_cast<unsigned long long>(clock64() - td));
         ptx::tc_fence_before();
         ptx::mbar_arrive(mbempty + mb);
-        mb ^= 1;
+        if (!wide) mb ^= 1;                 // six pairs: one main chunk
         if (mb == 0) mph ^= 1u;
       }
       if (!ok) break;
@@ -1001,12 +1040,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       ptx::tc_fence_after();
       if (p.npairs > 1) {
+        // the correction sums: the CB buffer, or (six pairs) the two halves of the wide
+        // accumulator in order
+        const int nh = wide ? 2 : 1;
+        const uint32_t col0 = wide ? WIDE_COL : CB_COL;
+#pragma unroll 1
+        for (int h = 0; h < nh; ++h) {
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
-          float v[32];
-          ptx::tmem_ld_32x32b_x32(lane_base + CB_COL + static_cast<uint32_t>(c * 32), v);
+          for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            ptx::tmem_ld_32x32b_x32(
+                lane_base + col0 + static_cast<uint32_t>(h * BN + c * 32), v);
 #pragma unroll
-          for (int u = 0; u < 32; ++u) acc[c * 32 + u] += v[u];
+            for (int u = 0; u < 32; ++u) acc[c * 32 + u] += v[u];
+          }
         }
       }
       ptx::tc_fence_before();
@@ -1330,11 +1377,21 @@ __global__ void load_state_kernel(const double *__restrict__ U, int n, int ldp, 
 }  // namespace
 
 void tc_schedule(const PairSet &ps, TcGemmParams &g) {
-  // Tile load order: L0, R0, then whatever the next pair in order needs.
+  // Tile load order: L0, R0, then whatever the next pair in order needs; six pairs (whose
+  // corrections go out as 128x256 products over two adjacent R tiles) load L0, L1, L2, R0, R1, R2.
   int pos[2][3];
   for (int s = 0; s < 2; ++s)
     for (int t = 0; t < 3; ++t) pos[s][t] = -1;
   g.ntl = 0;
+  if (ps.npairs == 6) {
+    for (int s = 0; s < 2; ++s)
+      for (int t = 0; t < 3; ++t) {
+        pos[s][t] = g.ntl;
+        g.tl_side[g.ntl] = s;
+        g.tl_term[g.ntl] = t;
+        ++g.ntl;
+      }
+  }
   auto need = [&](int side, int term) {
     if (pos[side][term] < 0) {
       pos[side][term] = g.ntl;
