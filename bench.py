@@ -41,8 +41,8 @@ FP64_ITERS = 6            # float64 parareal iterations of this workload to tol 
                           # eigenvalue-space oracle's count; checked by the CPU test suite)
 # DRAM bytes of one fine-sweep GEMM launch of this workload: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of a 16-slice launch of the same kernel
-# (1.123 GB + 0.673 GB), scaled by the slice count (the RK4 state is streamed once per launch).
-TRAFFIC_BYTES_PER_LAUNCH = (1.123311e9 + 0.673005e9) * 64 / 16
+# (1.160 GB + 0.667 GB), scaled by the slice count (the RK4 state is streamed once per launch).
+TRAFFIC_BYTES_PER_LAUNCH = (1.160388e9 + 0.666944e9) * 64 / 16
 CONFIG = {
     "workload": "exp flow dX/dt=AX, X(0)=I, T=1; n=2048 symmetric, lam~U[-4,0], Haar Q; "
                 "N=64 slices, 64 RK4 steps/slice (F), 1 Euler step/slice (G)",
